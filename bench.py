@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Benchmark of UTF-16 toWellFormed / isWellFormed on GB300.
+
+One step = one pass of the whole hot path over one synthetic input: the
+fused out-of-place toWellFormed + first-error-index kernel (load, classify,
+fast check, pair fix, store, first-error reduction) over a 1 GiB UTF-16
+string (536,870,912 units, 70/20/8 mix with lone surrogates at 1e-2 per unit).
+Inputs are resident in HBM before the timed region; 1 GiB is far larger than
+the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank runs an independent
+replica on its own GPU (no data-path collective); `value` is the units all
+ranks processed / the slowest rank's time.
+
+`--impl reference` times the CPU oracle (the plain scalar C definition) on the
+host cores on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "toWellFormed input GB/s & % of HBM roofline; ragged-batch GB/s; serve p50/p99"
+UNIT = "GB/s"
+MAIN_LONE_RATE = 1e-2
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = ("single 1 GiB UTF-16 string (536,870,912 units), 70/20/8 ASCII/BMP/pair mix with lone surrogates "
+            "at 1e-2 per unit; out-of-place toWellFormed fused with the first-error index")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="skip the variant / ragged / e2e measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2601_06349_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[name]
+        if e.get("kernel_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_launches(torch, fn, steps, stream):
+    """CUDA-event time (ms) of `steps` back-to-back calls on `stream`."""
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end)
+
+
+# ----------------------------------------------------------- CPU oracle leg
+def cpu_oracle_step(u, out, threads):
+    import oracle
+    oracle.to_well_formed_threads(u, out=out, threads=threads)
+    return oracle.first_bad_threads(u, threads=threads)
+
+
+def cpu_baseline(u, budget_s=20.0):
+    """The oracle as it stands, on the host cores, on the main workload."""
+    import oracle
+    threads = os.cpu_count() or 1
+    out = np.empty_like(u)
+    t0 = time.perf_counter()
+    cpu_oracle_step(u, out, threads)
+    first = time.perf_counter() - t0
+    reps = max(1, min(10, int(budget_s * 0.6 / max(first, 1e-3))))
+    best = first
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        cpu_oracle_step(u, out, threads)
+        best = min(best, time.perf_counter() - t0)
+    # single thread on a bounded prefix
+    sample = u[: min(u.size, 64 << 20)]
+    out1 = np.empty_like(sample)
+    t0 = time.perf_counter()
+    oracle.to_well_formed_threads(sample, out=out1, threads=1)
+    oracle.first_bad_threads(sample, threads=1)
+    single = time.perf_counter() - t0
+    return {
+        "value": round(u.size * 2 / best / 1e9, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+        "sample": f"whole 1 GiB string, best of {reps + 1} passes (repair + first-error index) on {threads} threads",
+        "single_thread": {"value": round(sample.size * 2 / single / 1e9, 3), "unit": UNIT,
+                          "sample": f"first {sample.size} units, one pass, 1 thread"},
+    }
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    u = workloads.large_mixed(MAIN_LONE_RATE)
+    out = np.empty_like(u)
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_oracle_step(u, out, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_step(u, out, threads)
+    dt = time.perf_counter() - t0
+    value = args.steps * u.size * 2 / dt / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "units": int(u.size), "parallelism": "host threads"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "whole 1 GiB string per step (repair + first-error index)"},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+
+    # CPU baseline data first (threads only; no process pool is forked later).
+    u = workloads.large_mixed(MAIN_LONE_RATE)
+    n = int(u.size)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2601_06349_gb300 as wf
+    wf.init_device()
+    stream = torch.cuda.current_stream()
+
+    d_in = torch.from_numpy(u.view(np.int16)).cuda()
+    d_out = torch.empty_like(d_in)
+    fb = torch.empty(1, dtype=torch.int64, device="cuda")
+
+    def step():
+        wf.to_well_formed_first_bad(d_in, d_out, fb, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = time_launches(torch, step, args.steps, stream)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n * 2 / (ms_per_step * 1e-3) / 1e9  # input GB/s over all replicas
+
+    peak, peak_kind = measured_peaks()
+    per_rank_hbm = n * 4 / (ms_per_step * 1e-3) / 1e9
+    traffic = recorded_traffic("single_out_fb_1GiB")
+    roofline = {"bound": "hbm", "achieved": round(per_rank_hbm, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(per_rank_hbm / peak, 4), "peak_kind": peak_kind,
+                "frac_of_nominal_8tbs": round(per_rank_hbm / NOMINAL_HBM_GBS, 4),
+                "traffic": traffic, "algorithmic_bytes_per_launch": n * 4,
+                "kernel": "single_kernel<out-of-place, first-error, 16-byte stores, U=4>"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "units": n, "l2": "inputs larger than L2 (1 GiB per step), no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    fbv = int(fb.item())
+    line["first_bad"] = fbv
+
+    if not args.no_extras:
+        line["e2e"] = e2e_measure(torch, wf, u, args)
+        line["variants"] = variants(torch, wf, stream, d_in, d_out, u)
+        del d_in, d_out
+        torch.cuda.empty_cache()
+        line["ragged"] = ragged_measure(torch, wf, stream)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(u)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def e2e_measure(torch, wf, u, args):
+    """Same metric through the host-buffer entry point (pinned buffers):
+    H2D of the input and D2H of the result and first-error index inside."""
+    h_in = torch.from_numpy(u.view(np.int16)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    wf.to_well_formed_host(h_in, h_out)
+    steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        _, fbv = wf.to_well_formed_host(h_in, h_out)
+    dt = (time.perf_counter() - t0) / steps
+    chunk = int(os.environ.get("UTF16WF_HOST_CHUNK_UNITS", 4 << 20))
+    chunks = -(-u.size // chunk)
+    return {"value": round(u.size * 2 / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(u.size * 2),
+            "d2h_bytes_per_step": int(u.size * 2 + 8 * chunks), "ms_per_step": round(dt * 1e3, 3),
+            "api": "utf16_to_well_formed_host (pinned host buffers, 3-stream chunk pipeline)",
+            "first_bad": fbv}
+
+
+def variants(torch, wf, stream, d_in, d_out, u_main):
+    """The other single-string forms: GB/s of input and fraction of the HBM peak."""
+    peak, _ = measured_peaks()
+    res = {}
+
+    def rec(name, n, ms, bytes_per_unit):
+        res[name] = {"input_gbs": round(n * 2 / (ms * 1e-3) / 1e9, 1),
+                     "hbm_frac": round(n * bytes_per_unit / (ms * 1e-3) / 1e9 / peak, 4), "ms": round(ms, 4)}
+
+    steps = 5
+    n = u_main.size
+    pristine = d_in.clone()
+
+    def timed_inplace(buf, src, reps):
+        best = None
+        for _ in range(reps):
+            buf.copy_(src)
+            ms = time_launches(torch, lambda: wf.to_well_formed_(buf, stream=stream), 1, stream)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    # 1 GiB mixed at three lone rates
+    for rate in (0.0, 1e-6, 1e-2):
+        if rate == MAIN_LONE_RATE:
+            src = pristine
+        else:
+            src = torch.from_numpy(workloads.large_mixed(rate).view(np.int16)).cuda()
+        ms = time_launches(torch, lambda: wf.to_well_formed_first_bad(src, d_out, stream=stream), steps, stream) / steps
+        rec(f"1GiB_p{rate:g}_out_first_bad", n, ms, 4)
+        ms = time_launches(torch, lambda: wf.to_well_formed(src, d_out, stream=stream), steps, stream) / steps
+        rec(f"1GiB_p{rate:g}_out", n, ms, 4)
+        ms = timed_inplace(d_in, src, 3)
+        rec(f"1GiB_p{rate:g}_inplace", n, ms, 2)
+        ms = time_launches(torch, lambda: wf.first_error_index(src, stream=stream), steps, stream) / steps
+        rec(f"1GiB_p{rate:g}_is_well_formed", n, ms, 2)
+        if src is not pristine:
+            del src
+    # 512 MiB adversarial strings
+    na = workloads.ADVERSARIAL_UNITS
+    a_out = d_out[:na]
+    a_buf = d_in[:na]
+    for kind in ("uniform", "shifted", "all_high"):
+        src = torch.from_numpy(workloads.adversarial(kind).view(np.int16)).cuda()
+        ms = time_launches(torch, lambda: wf.to_well_formed(src, a_out, stream=stream), steps, stream) / steps
+        rec(f"512MiB_{kind}_out", na, ms, 4)
+        ms = timed_inplace(a_buf, src, 3)
+        rec(f"512MiB_{kind}_inplace", na, ms, 4)
+        del src
+    # 1 MiB mixed (L2-resident: launch-latency bound, labelled as such)
+    small = torch.from_numpy(workloads.small_mixed().view(np.int16)).cuda()
+    s_out = torch.empty_like(small)
+    ms = time_launches(torch, lambda: wf.to_well_formed_first_bad(small, s_out, stream=stream), 200, stream) / 200
+    rec("1MiB_mixed_out_first_bad_L2_resident", small.numel(), ms, 4)
+    d_in.copy_(pristine)
+    del pristine
+    return res
+
+
+def ragged_measure(torch, wf, stream):
+    """1,000,000-string log-normal batch: one persistent launch vs one plain
+    launch per string (a timed sample of the per-string launches)."""
+    units, offs = workloads.ragged_batch()
+    total = int(offs[-1])
+    d_u = torch.from_numpy(units.view(np.int16)).cuda()
+    d_o = torch.from_numpy(offs).cuda()
+    d_out = torch.empty_like(d_u)
+    fbb = torch.empty(offs.size - 1, dtype=torch.int64, device="cuda")
+    steps = 20
+    for _ in range(3):
+        wf.to_well_formed_batch(d_u, d_o, d_out, stream=stream)
+    ms = time_launches(torch, lambda: wf.to_well_formed_batch(d_u, d_o, d_out, stream=stream), steps, stream) / steps
+    ms_chk = time_launches(torch, lambda: wf.first_error_index_batch(d_u, d_o, fbb, stream=stream), steps,
+                           stream) / steps
+    peak, _ = measured_peaks()
+    algo = total * 4 + offs.size * 8
+    res = {"strings": int(offs.size - 1), "units": total,
+           "batch_input_gbs": round(total * 2 / (ms * 1e-3) / 1e9, 1),
+           "batch_hbm_frac": round(algo / (ms * 1e-3) / 1e9 / peak, 4), "batch_ms": round(ms, 4),
+           "check_input_gbs": round(total * 2 / (ms_chk * 1e-3) / 1e9, 1), "check_ms": round(ms_chk, 4)}
+    # per-string plain launches on a sample of consecutive strings
+    sample = 20000
+    lens = np.diff(offs[: sample + 1])
+    base_in, base_out = d_u.data_ptr(), d_out.data_ptr()
+    calls = [(base_in + 2 * int(offs[i]), base_out + 2 * int(offs[i]), int(lens[i]))
+             for i in range(sample) if lens[i] > 0]
+    sample_units = int(lens.sum())
+    c_fn = wf.lib().utf16_to_well_formed
+    import ctypes
+    h = ctypes.c_void_p(stream.cuda_stream)
+
+    def per_string():
+        for a, b, ln in calls:
+            c_fn(a, b, ln, h)
+
+    per_string()
+    ms_ps = time_launches(torch, per_string, 1, stream)
+    res["per_string_launch_sample"] = {"strings": sample, "units": sample_units, "ms": round(ms_ps, 3),
+                                      "input_gbs": round(sample_units * 2 / (ms_ps * 1e-3) / 1e9, 3),
+                                      "strings_per_s": round(sample / (ms_ps * 1e-3), 1)}
+    res["batch_strings_per_s"] = round((offs.size - 1) / (ms * 1e-3), 1)
+    return res
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * utf16wf -- UTF-16 toWellFormed / isWellFormed on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the shared library libutf16wf.so.  No C++ or framework types appear
+ * in any signature: buffers are plain pointers, sizes are int64_t counts of
+ * 16-bit code units, streams are CUDA stream handles.
+ *
+ * What is computed (Section 1 of "Fixing ill-formed UTF-16 strings with SIMD
+ * instructions", Clausecker and Lemire):
+ *   - a high surrogate is a unit in 0xD800-0xDBFF, a low surrogate a unit in
+ *     0xDC00-0xDFFF;
+ *   - a high surrogate not immediately followed by a low surrogate, and a low
+ *     surrogate not immediately preceded by a high surrogate, is mismatched;
+ *   - toWellFormed replaces every mismatched unit by U+FFFD (0xFFFD) and keeps
+ *     every other unit, so the length never changes;
+ *   - units before the first and after the last unit of a string are outside
+ *     it (Section 3.1: an input that starts with a low or ends with a high
+ *     surrogate has that unit replaced).  In a batch every string is on its
+ *     own: a high surrogate that ends one string stays unpaired even when the
+ *     next string starts with a low surrogate.
+ *   - the first-error index is the index of the first unit that toWellFormed
+ *     replaces, or n when the string is well formed (isWellFormed is
+ *     first_bad == n).  The paper does not define an index; this one counts
+ *     the unit itself, not the position of the Section 3.1 step-two flag
+ *     (which is one unit late for a lone high surrogate, Fig. 3).
+ *
+ * Code units are native-order uint16_t values (no byte-order mark handling).
+ *
+ * Conventions for every entry point:
+ *   - Pointers are DEVICE pointers unless the name or comment says host.  A
+ *     buffer of code units must be 2-byte aligned; no other alignment is
+ *     required (16-byte aligned buffers are fastest).
+ *   - The caller owns every buffer.  The library never frees caller memory.
+ *     It keeps a small per-device scratch area (one 32-byte slot per stream
+ *     that has run a first-error computation, from a pool of 4096 slots) and,
+ *     for the host-memory entry point, staging buffers; both live until
+ *     process exit or utf16_release_device().
+ *   - Calls are asynchronous on `stream` unless stated otherwise.  Argument
+ *     errors are detected on the host before anything is launched and return
+ *     a negative status; CUDA errors of the launch return UTF16_ECUDA.  Errors
+ *     of the kernel itself surface at the next synchronising call, as in the
+ *     CUDA runtime.
+ *   - n == 0 (or an empty batch) is a valid no-op; first-error outputs are
+ *     then 0.
+ *   - `stream` may be NULL (the legacy default stream).  Calls that compute a
+ *     first-error index on the same stream are ordered; calls on different
+ *     streams use different scratch slots and may run concurrently.
+ */
+#ifndef UTF16WF_H
+#define UTF16WF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *utf16_stream_t;
+
+/* Status codes. */
+#define UTF16_OK 0
+#define UTF16_EINVAL (-1)   /* null pointer, negative size, misaligned buffer, bad offsets */
+#define UTF16_EOVERLAP (-2) /* in and out overlap without being the same buffer */
+#define UTF16_ECUDA (-3)    /* a CUDA call failed */
+#define UTF16_ETIMEOUT (-4) /* a bounded wait gave up (serving queue) */
+#define UTF16_ENOMEM (-5)   /* scratch slots, staging memory or serving budget exhausted */
+#define UTF16_ECLOSED (-6)  /* the serving engine is shut down */
+#define UTF16_EAGAIN (-7)   /* nothing ready yet (non-blocking poll) */
+
+/* Human-readable text of a status code (static storage, never NULL). */
+const char *utf16_strerror(int code);
+
+/*
+ * toWellFormed, out of place (Section 1 rule; Section 3.1 string ends).
+ *   in   [n] device, read.
+ *   out  [n] device, written: out[i] = 0xFFFD where in[i] is mismatched,
+ *        in[i] otherwise.  out == in is allowed (same as the in-place entry
+ *        point); any other overlap returns UTF16_EOVERLAP.
+ */
+int utf16_to_well_formed(const uint16_t *in, uint16_t *out, int64_t n, utf16_stream_t stream);
+
+/*
+ * toWellFormed in place.  Only 16-byte blocks that contain a mismatched unit
+ * are written; a well-formed string causes no stores at all (Section 3.1:
+ * in-place operation omits the copy).  Safe without inter-block ordering
+ * because replacing a mismatched unit by 0xFFFD never changes the verdict of
+ * a neighbour.
+ *   buf  [n] device, read and written.
+ */
+int utf16_to_well_formed_inplace(uint16_t *buf, int64_t n, utf16_stream_t stream);
+
+/*
+ * toWellFormed out of place (or in place when out == in) fused with the
+ * first-error index in the same pass.
+ *   first_bad  one int64_t, device or host pointer.  Device: written
+ *              asynchronously in stream order.  Host: the call waits for the
+ *              stream and returns with *first_bad set.
+ */
+int utf16_to_well_formed_first_bad(const uint16_t *in, uint16_t *out, int64_t n, int64_t *first_bad,
+                                   utf16_stream_t stream);
+
+/*
+ * isWellFormed with the first-error index; reads the string, writes nothing
+ * else.  Blocks stop early once a smaller error index is known.
+ *   first_bad  one int64_t, device or host pointer (as above).  Set to the
+ *              index of the first mismatched unit, or n if there is none.
+ */
+int utf16_is_well_formed(const uint16_t *in, int64_t n, int64_t *first_bad, utf16_stream_t stream);
+
+/*
+ * Ragged batch forms.  String s is in[offsets[s] .. offsets[s+1]) for
+ * s = 0 .. num_strings-1.
+ *   offsets    [num_strings + 1] int64, DEVICE, non-decreasing, offsets[0] >= 0
+ *              (it need not be 0).  The library reads the range from the
+ *              device, so a call never synchronises with the host.  Offsets
+ *              that decrease give unspecified (but memory-safe within
+ *              [offsets[0], offsets[num_strings]) output.
+ *   in, out    device buffers indexed by the offsets; only units in
+ *              [offsets[0], offsets[num_strings]) are read or written.
+ * Each string is repaired on its own: its first unit has no left neighbour
+ * and its last unit no right neighbour.
+ */
+int utf16_to_well_formed_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t num_strings,
+                               utf16_stream_t stream);
+int utf16_to_well_formed_batch_inplace(uint16_t *buf, const int64_t *offsets, int64_t num_strings,
+                                       utf16_stream_t stream);
+/*
+ *   first_bad  [num_strings] int64, DEVICE: first-error index of each string
+ *              relative to its start, equal to its length when well formed.
+ */
+int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64_t num_strings,
+                               int64_t *first_bad, utf16_stream_t stream);
+
+/*
+ * toWellFormed plus first-error index on HOST buffers.  The string is cut
+ * into chunks that are copied to the device, repaired and copied back on
+ * three library-owned streams so that the two copy directions and the kernel
+ * overlap; each chunk receives its outside neighbours from the host buffer,
+ * so the result is that of the whole string.  Blocking: returns when host_out
+ * holds the result.  Pinned (page-locked) host buffers give full overlap;
+ * pageable ones work but serialise the copies.
+ *   host_in, host_out  [n] host; host_out == host_in is allowed.
+ *   first_bad_host     one int64_t on the host, or NULL.
+ */
+int utf16_to_well_formed_host(const uint16_t *host_in, uint16_t *host_out, int64_t n, int64_t *first_bad_host);
+
+/*
+ * Prepare the current device (SM count, occupancy, scratch pool, launch
+ * tuning).  Called implicitly by the first entry point that needs it; call it
+ * explicitly before capturing a stream into a CUDA graph, since it allocates.
+ */
+int utf16_init_device(void);
+
+/* Free the current device's scratch and staging memory (after a device sync). */
+int utf16_release_device(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UTF16WF_H */

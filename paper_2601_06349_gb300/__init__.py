@@ -1,0 +1,251 @@
+"""utf16wf on GB300: UTF-16 toWellFormed / isWellFormed as CUDA kernels.
+
+Thin Python binding over the C ABI of ``libutf16wf.so`` (declared in
+``include/utf16wf.h``).  Every step of repair and validation runs in the CUDA
+kernels of that library; this module only marshals tensors (device memory
+and streams come from PyTorch) and raises on error status codes.  There is no
+CPU fallback: importing the functions without the built library raises.
+
+Code units are 16-bit tensors (``torch.uint16`` or ``torch.int16``, the bit
+pattern is what counts), contiguous, on a CUDA device.  Offsets of ragged
+batches are ``torch.int64`` CUDA tensors with ``num_strings + 1`` entries.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libutf16wf.so")
+
+OK, EINVAL, EOVERLAP, ECUDA, ETIMEOUT, ENOMEM, ECLOSED, EAGAIN = 0, -1, -2, -3, -4, -5, -6, -7
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Utf16Error(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (status {code})")
+
+
+def _declare(lib):
+    c_u16p = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    vp = ctypes.c_void_p
+    sig = {
+        "utf16_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "utf16_to_well_formed": ([vp, vp, i64, vp], ctypes.c_int),
+        "utf16_to_well_formed_inplace": ([vp, i64, vp], ctypes.c_int),
+        "utf16_to_well_formed_first_bad": ([vp, vp, i64, vp, vp], ctypes.c_int),
+        "utf16_is_well_formed": ([vp, i64, vp, vp], ctypes.c_int),
+        "utf16_to_well_formed_batch": ([vp, vp, vp, i64, vp], ctypes.c_int),
+        "utf16_to_well_formed_batch_inplace": ([vp, vp, i64, vp], ctypes.c_int),
+        "utf16_is_well_formed_batch": ([vp, vp, i64, vp, vp], ctypes.c_int),
+        "utf16_to_well_formed_host": ([c_u16p, c_u16p, i64, vp], ctypes.c_int),
+        "utf16_init_device": ([], ctypes.c_int),
+        "utf16_release_device": ([], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+def lib():
+    """The loaded C library (ctypes).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                                      "`python -m paper_2601_06349_gb300.build` (needs nvcc)")
+                _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().utf16_strerror(code).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise Utf16Error(rc, where)
+
+
+# ---------------------------------------------------------------- tensors
+def _torch():
+    import torch
+    return torch
+
+
+def _units(t, name="units"):
+    torch = _torch()
+    if t.dtype not in (torch.uint16, torch.int16):
+        raise TypeError(f"{name} must be torch.uint16 or torch.int16, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _stream(stream, device):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def to_well_formed(inp, out=None, *, stream=None):
+    """Repaired copy of ``inp`` (or into ``out``; ``out`` may be ``inp``)."""
+    torch = _torch()
+    _units(inp, "inp")
+    if out is None:
+        out = torch.empty_like(inp)
+    _units(out, "out")
+    if out.numel() != inp.numel():
+        raise ValueError("out must have as many units as inp")
+    with torch.cuda.device(inp.device):
+        _check(lib().utf16_to_well_formed(inp.data_ptr(), out.data_ptr(), inp.numel(),
+                                          _stream(stream, inp.device)), "utf16_to_well_formed")
+    return out
+
+
+def to_well_formed_(buf, *, stream=None):
+    """Repair ``buf`` in place (stores only 16-byte blocks that change)."""
+    torch = _torch()
+    _units(buf, "buf")
+    with torch.cuda.device(buf.device):
+        _check(lib().utf16_to_well_formed_inplace(buf.data_ptr(), buf.numel(), _stream(stream, buf.device)),
+               "utf16_to_well_formed_inplace")
+    return buf
+
+
+def to_well_formed_first_bad(inp, out=None, first_bad=None, *, stream=None):
+    """Repair and first-error index in one pass.  Returns (out, first_bad),
+    ``first_bad`` a one-element int64 CUDA tensor written in stream order."""
+    torch = _torch()
+    _units(inp, "inp")
+    if out is None:
+        out = torch.empty_like(inp)
+    _units(out, "out")
+    if first_bad is None:
+        first_bad = torch.empty(1, dtype=torch.int64, device=inp.device)
+    with torch.cuda.device(inp.device):
+        _check(lib().utf16_to_well_formed_first_bad(inp.data_ptr(), out.data_ptr(), inp.numel(),
+                                                    first_bad.data_ptr(), _stream(stream, inp.device)),
+               "utf16_to_well_formed_first_bad")
+    return out, first_bad
+
+
+def first_error_index(inp, first_bad=None, *, stream=None):
+    """isWellFormed: one-element int64 CUDA tensor (asynchronous) holding the
+    index of the first mismatched unit, or len(inp)."""
+    torch = _torch()
+    _units(inp, "inp")
+    if first_bad is None:
+        first_bad = torch.empty(1, dtype=torch.int64, device=inp.device)
+    with torch.cuda.device(inp.device):
+        _check(lib().utf16_is_well_formed(inp.data_ptr(), inp.numel(), first_bad.data_ptr(),
+                                          _stream(stream, inp.device)), "utf16_is_well_formed")
+    return first_bad
+
+
+def first_error_index_sync(inp, *, stream=None) -> int:
+    """isWellFormed with a host result (the call waits for the stream)."""
+    torch = _torch()
+    _units(inp, "inp")
+    v = ctypes.c_int64(-1)
+    with torch.cuda.device(inp.device):
+        _check(lib().utf16_is_well_formed(inp.data_ptr(), inp.numel(), ctypes.addressof(v),
+                                          _stream(stream, inp.device)), "utf16_is_well_formed")
+    return v.value
+
+
+def is_well_formed(inp, *, stream=None) -> bool:
+    return first_error_index_sync(inp, stream=stream) == inp.numel()
+
+
+def _offsets(offsets):
+    torch = _torch()
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous int64 CUDA tensor")
+    return offsets
+
+
+def to_well_formed_batch(units, offsets, out=None, *, stream=None):
+    """Repair each string units[offsets[s]:offsets[s+1]] on its own."""
+    torch = _torch()
+    _units(units)
+    _offsets(offsets)
+    if out is None:
+        out = units.clone()
+    _units(out, "out")
+    with torch.cuda.device(units.device):
+        _check(lib().utf16_to_well_formed_batch(units.data_ptr(), out.data_ptr(), offsets.data_ptr(),
+                                                offsets.numel() - 1, _stream(stream, units.device)),
+               "utf16_to_well_formed_batch")
+    return out
+
+
+def to_well_formed_batch_(units, offsets, *, stream=None):
+    torch = _torch()
+    _units(units)
+    _offsets(offsets)
+    with torch.cuda.device(units.device):
+        _check(lib().utf16_to_well_formed_batch_inplace(units.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
+                                                        _stream(stream, units.device)),
+               "utf16_to_well_formed_batch_inplace")
+    return units
+
+
+def first_error_index_batch(units, offsets, first_bad=None, *, stream=None):
+    """Per-string first-error index relative to each string (its length when
+    well formed), as an int64 CUDA tensor."""
+    torch = _torch()
+    _units(units)
+    _offsets(offsets)
+    count = offsets.numel() - 1
+    if first_bad is None:
+        first_bad = torch.empty(max(count, 0), dtype=torch.int64, device=units.device)
+    with torch.cuda.device(units.device):
+        _check(lib().utf16_is_well_formed_batch(units.data_ptr(), offsets.data_ptr(), count, first_bad.data_ptr(),
+                                                _stream(stream, units.device)), "utf16_is_well_formed_batch")
+    return first_bad
+
+
+def to_well_formed_host(host_in, host_out=None):
+    """Repair a host (CPU) buffer through the device; returns (out, first_bad).
+    ``host_in`` / ``host_out``: CPU tensors of 16-bit units (pinned memory
+    gives full copy/compute overlap) or numpy uint16 arrays."""
+    import numpy as np
+    if isinstance(host_in, np.ndarray):
+        if host_in.dtype != np.uint16 or not host_in.flags.c_contiguous:
+            raise TypeError("host_in must be a contiguous uint16 array")
+        if host_out is None:
+            host_out = np.empty_like(host_in)
+        pin, pout, n = host_in.ctypes.data, host_out.ctypes.data, host_in.size
+    else:
+        torch = _torch()
+        if host_in.is_cuda or host_in.dtype not in (torch.uint16, torch.int16):
+            raise TypeError("host_in must be a CPU tensor of 16-bit units")
+        if host_out is None:
+            host_out = torch.empty_like(host_in, pin_memory=host_in.is_pinned())
+        pin, pout, n = host_in.data_ptr(), host_out.data_ptr(), host_in.numel()
+    fb = ctypes.c_int64(-1)
+    _check(lib().utf16_to_well_formed_host(ctypes.c_void_p(pin), ctypes.c_void_p(pout), n, ctypes.addressof(fb)),
+           "utf16_to_well_formed_host")
+    return host_out, fb.value
+
+
+def init_device():
+    _check(lib().utf16_init_device(), "utf16_init_device")
+
+
+def release_device():
+    _check(lib().utf16_release_device(), "utf16_release_device")

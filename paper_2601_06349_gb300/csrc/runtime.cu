@@ -1,0 +1,296 @@
+// Host runtime of libutf16wf: per-device context (SM count, occupancy-derived
+// persistent grid sizes, scratch slots, staging for host buffers), argument
+// validation and the C-ABI entry points declared in include/utf16wf.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/utf16wf.h"
+#include "device.cuh"
+#include "internal.h"
+#include "runtime.h"
+
+namespace u16wf {
+
+static std::mutex g_mu;
+static std::unordered_map<int, std::unique_ptr<DeviceCtx>> g_ctx;
+
+static int env_int(const char *name, int dflt) {
+    const char *s = getenv(name);
+    if (!s || !*s) return dflt;
+    return atoi(s);
+}
+
+int DeviceCtx::blocks_for(const void *fn) {
+    auto it = occupancy.find(fn);
+    if (it != occupancy.end()) return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlockThreads, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int blocks = per_sm * sms;
+    occupancy[fn] = blocks;
+    return blocks;
+}
+
+int DeviceCtx::slot_for(cudaStream_t s, Slot **out) {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = slot_of.find(s);
+    if (it != slot_of.end()) {
+        *out = slots + it->second;
+        return UTF16_OK;
+    }
+    if (slots_used >= kSlotCount) return UTF16_ENOMEM;
+    const int idx = slots_used++;
+    slot_of[s] = idx;
+    *out = slots + idx;
+    return UTF16_OK;
+}
+
+int get_ctx(DeviceCtx **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ctx.find(dev);
+    if (it != g_ctx.end()) {
+        *out = it->second.get();
+        return UTF16_OK;
+    }
+    std::unique_ptr<DeviceCtx> c(new DeviceCtx());
+    c->device = dev;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    if (cudaMalloc((void **)&c->slots, sizeof(Slot) * kSlotCount) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ENOMEM;
+    }
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return UTF16_ECUDA;
+    if (init_slots(c->slots, kSlotCount, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return UTF16_ECUDA;
+    }
+    cudaStreamDestroy(s);
+    c->single_u = std::max(1, std::min(4, env_int("UTF16WF_SINGLE_U", 4)));
+    c->batch_u = std::max(1, std::min(4, env_int("UTF16WF_BATCH_U", 4)));
+    *out = c.get();
+    g_ctx[dev] = std::move(c);
+    return UTF16_OK;
+}
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static bool overlaps(const void *a, const void *b, int64_t n) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    const uintptr_t bytes = (uintptr_t)n * 2u;
+    return x != y && x < y + bytes && y < x + bytes;
+}
+
+static bool misaligned(const void *p) { return ((uintptr_t)p & 1u) != 0; }
+
+int run_single(const uint16_t *in, uint16_t *out, int64_t n, int mode, int64_t *first_bad, cudaStream_t stream,
+               uint32_t lead, uint32_t trail) {
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    const bool fb = first_bad != nullptr || mode == kModeCheck;
+    const bool fb_on_device = fb && first_bad && is_device_ptr(first_bad);
+    Slot *slot = nullptr;
+    if (fb) {
+        rc = ctx->slot_for(stream, &slot);
+        if (rc) return rc;
+    }
+    SingleLaunch L;
+    L.in = in;
+    L.out = out;
+    L.n = n;
+    L.mode = mode;
+    L.first_bad = fb;
+    L.units_per_thread = ctx->single_u;
+    L.max_blocks = ctx->blocks_for(single_kernel_for_occupancy(mode, fb, ctx->single_u));
+    L.slot = slot;
+    L.result = fb ? (fb_on_device ? (long long *)first_bad : &slot->result) : nullptr;
+    L.lead = lead;
+    L.trail = trail;
+    if (launch_single(L, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    if (fb && first_bad && !fb_on_device) {
+        if (cudaMemcpyAsync(first_bad, &slot->result, sizeof(int64_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+    }
+    return UTF16_OK;
+}
+
+static int empty_first_bad(int64_t *first_bad, cudaStream_t stream) {
+    if (!first_bad) return UTF16_OK;
+    if (is_device_ptr(first_bad)) {
+        if (cudaMemsetAsync(first_bad, 0, sizeof(int64_t), stream) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+    } else {
+        *first_bad = 0;
+    }
+    return UTF16_OK;
+}
+
+int run_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t count, int mode, int64_t *first_bad,
+              cudaStream_t stream, int units_per_thread) {
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    BatchLaunch L;
+    L.in = in;
+    L.out = out;
+    L.offsets = (const long long *)offsets;
+    L.count = count;
+    L.first_bad = (long long *)first_bad;
+    L.mode = mode;
+    L.units_per_thread = units_per_thread > 0 ? units_per_thread : ctx->batch_u;
+    L.blocks = ctx->blocks_for(batch_kernel_for_occupancy(mode, L.units_per_thread));
+    if (launch_batch(L, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    return UTF16_OK;
+}
+
+}  // namespace u16wf
+
+using namespace u16wf;
+
+extern "C" {
+
+const char *utf16_strerror(int code) {
+    switch (code) {
+        case UTF16_OK: return "success";
+        case UTF16_EINVAL: return "invalid argument (null pointer, negative size, misaligned buffer or bad offsets)";
+        case UTF16_EOVERLAP: return "input and output overlap without being the same buffer";
+        case UTF16_ECUDA: return "a CUDA call failed";
+        case UTF16_ETIMEOUT: return "a bounded wait gave up";
+        case UTF16_ENOMEM: return "out of scratch slots, staging memory or serving budget";
+        case UTF16_ECLOSED: return "the serving engine is shut down";
+        case UTF16_EAGAIN: return "nothing ready yet";
+        default: return "unknown status code";
+    }
+}
+
+int utf16_init_device(void) {
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    for (int mode = 0; mode < 3; ++mode) {
+        ctx->blocks_for(single_kernel_for_occupancy(mode, true, ctx->single_u));
+        ctx->blocks_for(single_kernel_for_occupancy(mode, false, ctx->single_u));
+        ctx->blocks_for(batch_kernel_for_occupancy(mode, ctx->batch_u));
+    }
+    return UTF16_OK;
+}
+
+int utf16_release_device(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    std::unique_ptr<DeviceCtx> c;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_ctx.find(dev);
+        if (it == g_ctx.end()) return UTF16_OK;
+        c = std::move(it->second);
+        g_ctx.erase(it);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    c->release_staging();
+    if (c->slots) cudaFree(c->slots);
+    c->slots = nullptr;
+    return UTF16_OK;
+}
+
+int utf16_to_well_formed(const uint16_t *in, uint16_t *out, int64_t n, utf16_stream_t stream) {
+    if (n < 0) return UTF16_EINVAL;
+    if (n == 0) return UTF16_OK;
+    if (!in || !out || misaligned(in) || misaligned(out)) return UTF16_EINVAL;
+    if (overlaps(in, out, n)) return UTF16_EOVERLAP;
+    return run_single(in, out, n, in == out ? kModeInPlace : kModeOut, nullptr, (cudaStream_t)stream, 0, 0);
+}
+
+int utf16_to_well_formed_inplace(uint16_t *buf, int64_t n, utf16_stream_t stream) {
+    if (n < 0) return UTF16_EINVAL;
+    if (n == 0) return UTF16_OK;
+    if (!buf || misaligned(buf)) return UTF16_EINVAL;
+    return run_single(buf, buf, n, kModeInPlace, nullptr, (cudaStream_t)stream, 0, 0);
+}
+
+int utf16_to_well_formed_first_bad(const uint16_t *in, uint16_t *out, int64_t n, int64_t *first_bad,
+                                   utf16_stream_t stream) {
+    if (n < 0 || !first_bad) return UTF16_EINVAL;
+    if (n == 0) return empty_first_bad(first_bad, (cudaStream_t)stream);
+    if (!in || !out || misaligned(in) || misaligned(out)) return UTF16_EINVAL;
+    if (overlaps(in, out, n)) return UTF16_EOVERLAP;
+    return run_single(in, out, n, in == out ? kModeInPlace : kModeOut, first_bad, (cudaStream_t)stream, 0, 0);
+}
+
+int utf16_is_well_formed(const uint16_t *in, int64_t n, int64_t *first_bad, utf16_stream_t stream) {
+    if (n < 0 || !first_bad) return UTF16_EINVAL;
+    if (n == 0) return empty_first_bad(first_bad, (cudaStream_t)stream);
+    if (!in || misaligned(in)) return UTF16_EINVAL;
+    return run_single(in, nullptr, n, kModeCheck, first_bad, (cudaStream_t)stream, 0, 0);
+}
+
+int utf16_to_well_formed_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t num_strings,
+                               utf16_stream_t stream) {
+    if (num_strings < 0) return UTF16_EINVAL;
+    if (num_strings == 0) return UTF16_OK;
+    if (!in || !out || !offsets || misaligned(in) || misaligned(out) || ((uintptr_t)offsets & 7u)) return UTF16_EINVAL;
+    return run_batch(in, out, offsets, num_strings, in == out ? kModeInPlace : kModeOut, nullptr,
+                     (cudaStream_t)stream, 0);
+}
+
+int utf16_to_well_formed_batch_inplace(uint16_t *buf, const int64_t *offsets, int64_t num_strings,
+                                       utf16_stream_t stream) {
+    if (num_strings < 0) return UTF16_EINVAL;
+    if (num_strings == 0) return UTF16_OK;
+    if (!buf || !offsets || misaligned(buf) || ((uintptr_t)offsets & 7u)) return UTF16_EINVAL;
+    return run_batch(buf, buf, offsets, num_strings, kModeInPlace, nullptr, (cudaStream_t)stream, 0);
+}
+
+int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64_t num_strings, int64_t *first_bad,
+                               utf16_stream_t stream) {
+    if (num_strings < 0) return UTF16_EINVAL;
+    if (num_strings == 0) return UTF16_OK;
+    if (!in || !offsets || !first_bad || misaligned(in) || ((uintptr_t)offsets & 7u) || ((uintptr_t)first_bad & 7u))
+        return UTF16_EINVAL;
+    return run_batch(in, nullptr, offsets, num_strings, kModeCheck, first_bad, (cudaStream_t)stream, 0);
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// Host-side runtime state shared by the entry points (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <unordered_map>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace u16wf {
+
+constexpr int kSlotCount = 4096;
+constexpr int kHostLanes = 3;
+
+struct DeviceCtx {
+    int device = 0;
+    int sms = 1;
+    int single_u = 4;
+    int batch_u = 4;
+    std::mutex mu;
+    Slot *slots = nullptr;  // device pool of kSlotCount slots
+    int slots_used = 0;
+    std::unordered_map<cudaStream_t, int> slot_of;
+    std::unordered_map<const void *, int> occupancy;  // kernel -> persistent grid size
+
+    // Host-buffer pipeline: kHostLanes streams, each with a device staging
+    // buffer of `stage_units` units; pinned per-chunk first-error results.
+    std::mutex stage_mu;
+    cudaStream_t lanes[kHostLanes] = {nullptr, nullptr, nullptr};
+    uint16_t *stage[kHostLanes] = {nullptr, nullptr, nullptr};
+    int64_t stage_units = 0;
+    int64_t *chunk_first = nullptr;  // pinned host
+    int64_t chunk_first_cap = 0;
+
+    int blocks_for(const void *fn);
+    int slot_for(cudaStream_t s, Slot **out);
+    int ensure_staging(int64_t units, int64_t chunks);
+    void release_staging();
+};
+
+int get_ctx(DeviceCtx **out);
+
+// Single-string launch with optional first-error output (host or device
+// pointer) and outside neighbours `lead` / `trail` (0 = none).
+int run_single(const uint16_t *in, uint16_t *out, int64_t n, int mode, int64_t *first_bad, cudaStream_t stream,
+               uint32_t lead, uint32_t trail);
+
+int run_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t count, int mode, int64_t *first_bad,
+              cudaStream_t stream, int units_per_thread);
+
+}  // namespace u16wf

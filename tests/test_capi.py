@@ -1,0 +1,97 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/utf16wf.h declares; argument errors are rejected on the host before
+any CUDA call (these tests run without a GPU and make no compute call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(HEADER_DIR)):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(HEADER_DIR, h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(utf16_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2601_06349_gb300 import build
+    build.build()
+    import paper_2601_06349_gb300 as pkg
+    return pkg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("utf16_to_well_formed", "utf16_to_well_formed_inplace", "utf16_is_well_formed",
+                     "utf16_to_well_formed_batch", "utf16_to_well_formed_batch_inplace",
+                     "utf16_is_well_formed_batch", "utf16_strerror", "utf16_to_well_formed_host"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(capi):
+    missing = [n for n in declared_functions() if not hasattr(capi, n)]
+    assert not missing, missing
+
+
+def test_strerror(capi):
+    import paper_2601_06349_gb300 as pkg
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, 12345):
+        s = pkg.strerror(code)
+        assert isinstance(s, str) and s
+
+
+def test_argument_errors_before_any_cuda_call(capi):
+    vp = ctypes.c_void_p
+    # negative sizes
+    assert capi.utf16_to_well_formed(vp(16), vp(4096), -1, None) == -1
+    assert capi.utf16_to_well_formed_inplace(vp(16), -5, None) == -1
+    # null buffers with n > 0
+    assert capi.utf16_to_well_formed(None, vp(4096), 10, None) == -1
+    assert capi.utf16_to_well_formed(vp(4096), None, 10, None) == -1
+    assert capi.utf16_to_well_formed_inplace(None, 10, None) == -1
+    # odd (not 2-byte aligned) buffers
+    assert capi.utf16_to_well_formed(vp(4097), vp(8192), 10, None) == -1
+    # partial overlap
+    assert capi.utf16_to_well_formed(vp(4096), vp(4098), 10, None) == -2
+    # missing first-error output
+    assert capi.utf16_is_well_formed(vp(4096), 10, None, None) == -1
+    assert capi.utf16_to_well_formed_first_bad(vp(4096), vp(8192), 10, None, None) == -1
+    # batch: negative count, null offsets, misaligned offsets
+    assert capi.utf16_to_well_formed_batch(vp(4096), vp(8192), vp(64), -1, None) == -1
+    assert capi.utf16_to_well_formed_batch(vp(4096), vp(8192), None, 3, None) == -1
+    assert capi.utf16_to_well_formed_batch(vp(4096), vp(8192), vp(65), 3, None) == -1
+    assert capi.utf16_is_well_formed_batch(vp(4096), vp(64), 3, None, None) == -1
+    # host entry point
+    assert capi.utf16_to_well_formed_host(None, None, 3, None) == -1
+
+
+def test_empty_inputs_are_noops(capi):
+    vp = ctypes.c_void_p
+    assert capi.utf16_to_well_formed(None, None, 0, None) == 0
+    assert capi.utf16_to_well_formed_inplace(None, 0, None) == 0
+    assert capi.utf16_to_well_formed_batch(None, None, None, 0, None) == 0
+    assert capi.utf16_to_well_formed_batch_inplace(None, None, 0, None) == 0
+    fb = ctypes.c_int64(-1)
+    assert capi.utf16_to_well_formed_host(None, None, 0, ctypes.addressof(fb)) == 0
+    assert fb.value == 0
+
+
+def test_binding_rejects_cpu_tensors(capi):
+    torch = pytest.importorskip("torch")
+    import paper_2601_06349_gb300 as pkg
+    with pytest.raises(ValueError):
+        pkg.to_well_formed(torch.zeros(4, dtype=torch.int16))
+    with pytest.raises(TypeError):
+        pkg.to_well_formed(torch.zeros(4, dtype=torch.float32))

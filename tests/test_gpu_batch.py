@@ -1,0 +1,114 @@
+"""Ragged-batch CUDA path against the per-string oracle, bit-exact, through
+the C ABI: every string of length <= 5 over the border alphabet as one batch
+(at several base misalignments and a nonzero first offset), the 1,000,000
+string log-normal batch, and degenerate batches (all empty, one string, runs
+of empty strings, strings longer than a chunk)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import CANARY, Guarded, first_diff
+from test_oracle import all_strings
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2601_06349_gb300 as p
+    p.init_device()
+    return p
+
+
+def _run_all_forms(pkg, units, offs, a_in=0, a_out=0, label=""):
+    """units: host array the offsets index; returns nothing, asserts parity."""
+    import torch
+    want = oracle.to_well_formed_batch(units, offs)
+    want_fb = oracle.first_bad_batch(units, offs)
+    lo, hi = int(offs[0]), int(offs[-1])
+    d_off = torch.from_numpy(offs).cuda()
+    gi = Guarded(units.size, a_in, units)
+    # out of place: units outside [lo, hi) of `out` must stay untouched
+    go = Guarded(units.size, a_out, np.full(units.size, CANARY, np.uint16))
+    pkg.to_well_formed_batch(gi.view, d_off, go.view)
+    got = go.get()
+    assert np.array_equal(got[lo:hi], want[lo:hi]), (label, a_in, a_out, first_diff(got[lo:hi], want[lo:hi]))
+    assert np.all(got[:lo] == CANARY) and np.all(got[hi:] == CANARY), label
+    assert go.canaries_ok()
+    # per-string first-error index
+    fb = pkg.first_error_index_batch(gi.view, d_off)
+    got_fb = fb.cpu().numpy()
+    assert np.array_equal(got_fb, want_fb), (label, first_diff(got_fb, want_fb))
+    assert np.array_equal(gi.get(), units)
+    # in place
+    gp = Guarded(units.size, a_in, units)
+    pkg.to_well_formed_batch_(gp.view, d_off)
+    got = gp.get()
+    assert np.array_equal(got, want), (label, first_diff(got, want))
+    assert gp.canaries_ok()
+
+
+@pytest.fixture(scope="module")
+def exhaustive_batch():
+    strings = list(all_strings())
+    lens = np.array([len(s) for s in strings], dtype=np.int64)
+    units = np.array([u for s in strings for u in s], dtype=np.uint16)
+    return units, lens
+
+
+@pytest.mark.parametrize("a_in,a_out", [(0, 0), (3, 3), (1, 6), (7, 2), (5, 4)])
+def test_exhaustive_alphabet_batch(pkg, exhaustive_batch, a_in, a_out):
+    units, lens = exhaustive_batch
+    offs = workloads.offsets_from_lengths(lens)
+    _run_all_forms(pkg, units, offs, a_in, a_out, "exhaustive")
+
+
+def test_exhaustive_batch_nonzero_start(pkg, exhaustive_batch):
+    units, lens = exhaustive_batch
+    pre = np.full(1001, 0xD800, np.uint16)  # outside the batch range: never read as neighbours
+    post = np.full(999, 0xDC00, np.uint16)
+    all_units = np.concatenate([pre, units, post])
+    offs = workloads.offsets_from_lengths(lens, start=pre.size)
+    _run_all_forms(pkg, all_units, offs, 2, 5, "exhaustive+start")
+
+
+def test_lognormal_batch_million_strings(pkg):
+    units, offs = workloads.ragged_batch()
+    assert offs.size == 1_000_001
+    _run_all_forms(pkg, units, offs, 0, 0, "ragged 1M")
+
+
+def test_degenerate_batches(pkg):
+    rng = np.random.default_rng(5)
+    alph = np.array([0x41, 0xD800, 0xDBFF, 0xDC00, 0xDFFF, 0xFFFD], np.uint16)
+    cases = []
+    # all empty
+    cases.append((np.full(10, 0xD800, np.uint16), np.full(50, 4, np.int64)))
+    # one string
+    u = alph[rng.integers(0, alph.size, 70_001)]
+    cases.append((u, np.array([0, u.size], np.int64)))
+    # runs of empty strings between short ones, and long strings spanning chunks
+    lens = []
+    for _ in range(3000):
+        r = rng.random()
+        lens.append(0 if r < 0.4 else (int(rng.integers(1, 8)) if r < 0.8 else int(rng.integers(900, 5000))))
+    lens = np.array(lens, np.int64)
+    offs = workloads.offsets_from_lengths(lens, start=3)
+    u = alph[rng.integers(0, alph.size, int(offs[-1]) + 5)]
+    cases.append((u, offs))
+    # every string length 1 (each surrogate is alone)
+    u = alph[rng.integers(0, alph.size, 20_000)]
+    cases.append((u, np.arange(u.size + 1, dtype=np.int64)))
+    for k, (u, offs) in enumerate(cases):
+        _run_all_forms(pkg, u, offs, k % 8, (3 * k) % 8, f"degenerate {k}")
+
+
+def test_batch_boundary_pairs(pkg):
+    # H | L across a string boundary stays unpaired; inside a string it pairs.
+    u = np.array([0x41, 0xD800, 0xDC00, 0xD800, 0xDC00, 0x42] * 1000, np.uint16)
+    lens = np.array([2, 1, 3] * 1000, np.int64)  # splits the first pair, keeps the second
+    offs = workloads.offsets_from_lengths(lens)
+    _run_all_forms(pkg, u, offs, 0, 0, "boundary pairs")

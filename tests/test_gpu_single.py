@@ -1,0 +1,225 @@
+"""Single-string CUDA path against the oracle, bit-exact (integer work: the
+tolerance is zero), through the C ABI.
+
+* a sweep of small lengths (0..70 and sizes around every tile edge) at every
+  misalignment of the input (0..7 units) and of the output relative to it,
+  with guard bands, for out-of-place, fused first-error, in-place and
+  read-only entry points, device and host first-error pointers;
+* the full-size strings in the launch configuration the benchmark times:
+  1 MiB mixed, 1 GiB mixed at lone rates 0 / 1e-6 / 1e-2, the three 512 MiB
+  adversarial strings;
+* isWellFormed's early exit, stream independence of the scratch slots, and
+  the pipelined host-buffer entry point (chunk edges inside surrogate pairs).
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import Guarded, first_diff, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+ALPHABET = np.array([0x0041, 0x00E9, 0xD7FF, 0xD800, 0xDBFF, 0xDC00, 0xDFFF, 0xE000, 0xFFFD, 0xFFFF], np.uint16)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2601_06349_gb300 as p
+    p.init_device()
+    return p
+
+
+def _sweep_sizes():
+    sizes = list(range(0, 71))
+    for edge in (256, 512, 1024, 2048, 4096, 8192, 65536):
+        sizes += [edge - 9, edge - 1, edge, edge + 1, edge + 9]
+    sizes += [100_003, 262_147]
+    return sorted(set(s for s in sizes if s >= 0))
+
+
+def _content(n, rng):
+    if n < 4096:
+        return ALPHABET[rng.integers(0, ALPHABET.size, n)]
+    u = workloads.mixed(n, 0.02, seed=int(rng.integers(1 << 30)))
+    # sprinkle surrogates so that every chunk takes the slow path somewhere
+    idx = rng.integers(0, n, n // 50)
+    u[idx] = ALPHABET[rng.integers(0, ALPHABET.size, idx.size)]
+    return u
+
+
+def test_small_sweep_all_alignments(pkg):
+    import torch
+    rng = np.random.default_rng(2026)
+    for n in _sweep_sizes():
+        offs = range(8) if n < 5000 else (0, 3)
+        for a_in in offs:
+            u = _content(n, rng)
+            want = oracle.to_well_formed(u)
+            want_fb = oracle.first_bad(u)
+            gi = Guarded(n, a_in, u)
+            for a_out in (range(8) if n < 300 else (a_in, (a_in + 1) % 8, (a_in + 4) % 8)):
+                go = Guarded(n, a_out)
+                pkg.to_well_formed(gi.view, go.view)
+                got = go.get()
+                assert np.array_equal(got, want), (n, a_in, a_out, first_diff(got, want))
+                assert go.canaries_ok(), (n, a_in, a_out)
+                go2 = Guarded(n, a_out)
+                _, fb = pkg.to_well_formed_first_bad(gi.view, go2.view)
+                assert np.array_equal(go2.get(), want), (n, a_in, a_out)
+                assert int(fb.item()) == want_fb, (n, a_in, a_out)
+                assert go2.canaries_ok()
+            # read-only check: device and host result pointers
+            assert int(pkg.first_error_index(gi.view).item()) == want_fb, (n, a_in)
+            assert pkg.first_error_index_sync(gi.view) == want_fb, (n, a_in)
+            assert np.array_equal(gi.get(), u)
+            assert gi.canaries_ok()
+            # in place
+            gp = Guarded(n, a_in, u)
+            pkg.to_well_formed_(gp.view)
+            assert np.array_equal(gp.get(), want), (n, a_in, first_diff(gp.get(), want))
+            assert gp.canaries_ok()
+    torch.cuda.synchronize()
+
+
+def test_in_place_same_pointer_via_out_of_place_entry(pkg):
+    u = workloads.mixed(300_001, 0.05, seed=5)
+    g = Guarded(u.size, 3, u)
+    pkg.to_well_formed(g.view, g.view)
+    assert np.array_equal(g.get(), oracle.to_well_formed(u))
+    assert g.canaries_ok()
+
+
+def _full_check(pkg, u, label):
+    import torch
+    want = oracle.to_well_formed_threads(u)
+    want_fb = oracle.first_bad_threads(u)
+    d_in = to_dev(u)
+    d_out = torch.empty_like(d_in)
+    # fused out-of-place + first-error (the benchmarked launch)
+    _, fb = pkg.to_well_formed_first_bad(d_in, d_out)
+    got = to_host(d_out)
+    assert np.array_equal(got, want), (label, first_diff(got, want))
+    assert int(fb.item()) == want_fb, label
+    # read-only
+    assert pkg.first_error_index_sync(d_in) == want_fb, label
+    # out-of-place without first-error
+    d_out.fill_(0)
+    pkg.to_well_formed(d_in, d_out)
+    assert np.array_equal(to_host(d_out), want), label
+    # in place (input no longer needed)
+    pkg.to_well_formed_(d_in)
+    got = to_host(d_in)
+    assert np.array_equal(got, want), (label, first_diff(got, want))
+    del d_in, d_out
+    torch.cuda.empty_cache()
+    return want_fb, int(np.count_nonzero(want != u))
+
+
+def test_small_mixed_string(pkg):
+    u = workloads.small_mixed()
+    fb, nbad = _full_check(pkg, u, "1 MiB mixed")
+    assert nbad > 0 and fb < 100
+
+
+@pytest.mark.parametrize("lone_rate", [0.0, 1e-6, 1e-2])
+def test_large_mixed_string(pkg, lone_rate):
+    u = workloads.large_mixed(lone_rate)
+    fb, nbad = _full_check(pkg, u, f"1 GiB mixed p={lone_rate}")
+    if lone_rate == 0.0:
+        assert nbad == 0 and fb == u.size
+
+
+@pytest.mark.parametrize("kind", ["uniform", "shifted", "all_high"])
+def test_adversarial_string(pkg, kind):
+    u = workloads.adversarial(kind)
+    fb, nbad = _full_check(pkg, u, kind)
+    if kind == "shifted":
+        assert nbad == 65_584 and fb == 4092
+    if kind == "all_high":
+        assert nbad == u.size and fb == 0
+
+
+def test_is_well_formed_early_exit_positions(pkg):
+    n = 50_000_000
+    base = workloads.mixed(n, 0.0, seed=17)
+    for pos in (0, 1, 255, 256, 1023, 1024, 12_345_678, n - 2, n - 1):
+        u = base.copy()
+        u[pos] = 0xDC00 if pos == 0 else 0xD800
+        if pos > 0 and 0xD800 <= u[pos - 1] <= 0xDBFF:
+            u[pos - 1] = 0x41  # keep the planted error the first one
+        want = oracle.first_bad(u)
+        d = to_dev(u)
+        assert pkg.first_error_index_sync(d) == want, pos
+        assert int(pkg.first_error_index(d).item()) == want, pos
+    d = to_dev(base)
+    assert pkg.first_error_index_sync(d) == n
+    assert pkg.is_well_formed(d)
+
+
+def test_streams_use_independent_slots(pkg):
+    import torch
+    strings = [workloads.mixed(3_000_000 + 7 * i, 1e-4 * (i + 1), seed=100 + i) for i in range(6)]
+    wants = [oracle.first_bad(s) for s in strings]
+    devs = [to_dev(s) for s in strings]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    results = []
+    for rep in range(3):
+        for i, d in enumerate(devs):
+            s = streams[i % 3]
+            with torch.cuda.stream(s):
+                results.append((i, pkg.first_error_index(d, stream=s)))
+    torch.cuda.synchronize()
+    for i, t in results:
+        assert int(t.item()) == wants[i]
+
+
+@pytest.mark.parametrize("chunk", [4096, 1 << 20])
+def test_host_pipeline_chunk_edges(pkg, chunk):
+    os.environ["UTF16WF_HOST_CHUNK_UNITS"] = str(chunk)
+    try:
+        for kind, u in (("shifted", workloads.shifted_alternating(3 * chunk + 77)),
+                        ("mixed", workloads.mixed(5 * chunk + 3, 0.01, seed=3)),
+                        ("uniform", workloads.uniform_surrogates(2 * chunk + 1, seed=4))):
+            want = oracle.to_well_formed(u)
+            out, fb = pkg.to_well_formed_host(u)
+            assert np.array_equal(out, want), (kind, first_diff(out, want))
+            assert fb == oracle.first_bad(u), kind
+            v = u.copy()
+            out2, fb2 = pkg.to_well_formed_host(v, v)  # in place on the host buffer
+            assert np.array_equal(v, want) and fb2 == fb, kind
+    finally:
+        os.environ.pop("UTF16WF_HOST_CHUNK_UNITS", None)
+
+
+def test_host_pipeline_pinned_large(pkg):
+    import torch
+    u = workloads.large_mixed(1e-2)
+    want = oracle.to_well_formed_threads(u)
+    h_in = torch.from_numpy(u.view(np.int16)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    out, fb = pkg.to_well_formed_host(h_in, h_out)
+    got = out.numpy().view(np.uint16)
+    assert np.array_equal(got, want), first_diff(got, want)
+    assert fb == oracle.first_bad_threads(u)
+
+
+def test_raw_c_abi_host_first_bad_pointer(pkg):
+    """Direct ctypes call: host first-error pointer makes the call blocking."""
+    import torch
+    u = workloads.mixed(777_777, 1e-3, seed=9)
+    d = to_dev(u)
+    v = ctypes.c_int64(-7)
+    rc = pkg.lib().utf16_is_well_formed(d.data_ptr(), u.size, ctypes.addressof(v),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0 and v.value == oracle.first_bad(u)
+    out = torch.empty_like(d)
+    w = ctypes.c_int64(-7)
+    rc = pkg.lib().utf16_to_well_formed_first_bad(d.data_ptr(), out.data_ptr(), u.size, ctypes.addressof(w), None)
+    assert rc == 0 and w.value == v.value
+    assert np.array_equal(to_host(out), oracle.to_well_formed(u))
