@@ -113,7 +113,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -266,9 +266,15 @@ def main():
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
+    soak_end = time.perf_counter() + 1.5  # untimed load so the sampler sees the clocks under this kernel
+    while time.perf_counter() < soak_end:
+        for _ in range(50):
+            step()
+        torch.cuda.synchronize()
     ms = time_launches(torch, step, args.steps, stream)
     clk = clocks.stop()
+    if clk is not None:
+        clk["window"] = "1.5 s untimed soak of the same step followed by the timed steps"
     if dist:
         dist.barrier()
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -347,6 +353,11 @@ def variants(torch, wf, stream, d_in, d_out, u_main):
     n = u_main.size
     pristine = d_in.clone()
 
+    def changed_units(src, out_buf):
+        wf.to_well_formed(src, out_buf, stream=stream)
+        torch.cuda.synchronize()
+        return int((out_buf != src).sum().item())
+
     def timed_inplace(buf, src, reps):
         best = None
         for _ in range(reps):
@@ -365,10 +376,14 @@ def variants(torch, wf, stream, d_in, d_out, u_main):
         rec(f"1GiB_p{rate:g}_out_first_bad", n, ms, 4)
         ms = time_launches(torch, lambda: wf.to_well_formed(src, d_out, stream=stream), steps, stream) / steps
         rec(f"1GiB_p{rate:g}_out", n, ms, 4)
+        ch = changed_units(src, d_out)
         ms = timed_inplace(d_in, src, 3)
-        rec(f"1GiB_p{rate:g}_inplace", n, ms, 2)
+        rec(f"1GiB_p{rate:g}_inplace", n, ms, 2 + 2 * ch / n)
+        res[f"1GiB_p{rate:g}_inplace"]["changed_units"] = ch
         ms = time_launches(torch, lambda: wf.first_error_index(src, stream=stream), steps, stream) / steps
         rec(f"1GiB_p{rate:g}_is_well_formed", n, ms, 2)
+        if ch:
+            res[f"1GiB_p{rate:g}_is_well_formed"]["note"] = "stops early at the first error"
         if src is not pristine:
             del src
     # 512 MiB adversarial strings
@@ -379,8 +394,10 @@ def variants(torch, wf, stream, d_in, d_out, u_main):
         src = torch.from_numpy(workloads.adversarial(kind).view(np.int16)).cuda()
         ms = time_launches(torch, lambda: wf.to_well_formed(src, a_out, stream=stream), steps, stream) / steps
         rec(f"512MiB_{kind}_out", na, ms, 4)
+        ch = changed_units(src, a_out)
         ms = timed_inplace(a_buf, src, 3)
-        rec(f"512MiB_{kind}_inplace", na, ms, 4)
+        rec(f"512MiB_{kind}_inplace", na, ms, 2 + 2 * ch / na)
+        res[f"512MiB_{kind}_inplace"]["changed_units"] = ch
         del src
     # 1 MiB mixed (L2-resident: launch-latency bound, labelled as such)
     small = torch.from_numpy(workloads.small_mixed().view(np.int16)).cuda()
