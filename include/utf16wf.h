@@ -67,6 +67,7 @@ typedef struct CUstream_st *utf16_stream_t;
 #define UTF16_ENOMEM (-5)   /* scratch slots, staging memory or serving budget exhausted */
 #define UTF16_ECLOSED (-6)  /* the serving engine is shut down */
 #define UTF16_EAGAIN (-7)   /* nothing ready yet (non-blocking poll) */
+#define UTF16_ETOOBIG (-8)  /* input longer than the no-allocation entry point's stated maximum */
 
 /* Human-readable text of a status code (static storage, never NULL). */
 const char *utf16_strerror(int code);
@@ -144,6 +145,28 @@ int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64
  *   first_bad_host     one int64_t on the host, or NULL.
  */
 int utf16_to_well_formed_host(const uint16_t *host_in, uint16_t *host_out, int64_t n, int64_t *first_bad_host);
+
+/*
+ * toWellFormed fused with the first-error index, allocating nothing.  The
+ * paper has no counterpart: this exists for callers that cannot let a library
+ * call cudaMalloc -- processes whose device memory is fully reserved by a
+ * host framework or a fixed budget, pipelines that forbid allocation after
+ * start-up, code that must not change the device's memory footprint.  Its
+ * only scratch is a 256-byte array compiled into the library (one 32-byte
+ * first-error slot), which every GPU that loads the library holds until the
+ * process exits.
+ *   in, out, n, first_bad, stream  as utf16_to_well_formed_first_bad (the
+ *                                  output is identical).
+ *   n must not exceed 2^40 units; longer inputs return UTF16_ETOOBIG.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before capturing a
+ * stream into a CUDA graph.  Every call shares the one array and keeps the
+ * last call's contents, clearing what must start cleared in stream order:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and may return wrong first-error indices.
+ */
+int utf16_to_well_formed_first_bad_noalloc(const uint16_t *in, uint16_t *out, int64_t n, int64_t *first_bad,
+                                           utf16_stream_t stream);
 
 /*
  * Prepare the current device (SM count, occupancy, scratch pool, launch

@@ -196,6 +196,7 @@ const char *utf16_strerror(int code) {
         case UTF16_ENOMEM: return "out of scratch slots, staging memory or serving budget";
         case UTF16_ECLOSED: return "the serving engine is shut down";
         case UTF16_EAGAIN: return "nothing ready yet";
+        case UTF16_ETOOBIG: return "input longer than the no-allocation entry point accepts (2^40 units)";
         default: return "unknown status code";
     }
 }
