@@ -169,6 +169,51 @@ int utf16_to_well_formed_first_bad_noalloc(const uint16_t *in, uint16_t *out, in
                                            utf16_stream_t stream);
 
 /*
+ * Launch configuration of the current device.  The kernels are the same in
+ * every configuration (results are identical); only speed changes.
+ */
+typedef struct {
+    int single_variant;          /* 0: 128-bit loads; 1: 128-bit loads, next chunk requested before the
+                                    current one is processed; 2: TMA bulk copies into a 4-stage
+                                    shared-memory ring (16 KiB tiles), repair only: the
+                                    read-only check then uses variant 0 */
+    int single_units_per_thread; /* 16-byte vectors per thread per warp chunk: 2 or 4 (TMA uses 4) */
+    int single_blocks_per_sm;    /* persistent grid = SMs x this; 0 = as many as fit */
+    int batch_units_per_thread;  /* 2 or 4 */
+    int batch_prefetch;          /* 0 or 1 */
+    int batch_blocks_per_sm;     /* 0 = as many as fit */
+} utf16_config;
+
+/* Default configuration of the current device (used where nothing is tuned). */
+int utf16_get_config(utf16_config *cfg);
+/* Replace the default configuration; clears all tuned entries.  Values out
+ * of range return UTF16_EINVAL. */
+int utf16_set_config(const utf16_config *cfg);
+
+/*
+ * Autotuner.  Times every candidate configuration (variant x units per thread
+ * x blocks per SM) on the caller's own device buffers with CUDA events,
+ * `reps` launches each after one warm-up, on a library stream; synchronous.
+ * The fastest is stored for the size bucket floor(log2(n)) of single strings
+ * (utf16_autotune_single, out-of-place repair with first-error index) or for
+ * the bucket floor(log2(num_strings)) of batches (utf16_autotune_batch, the
+ * out-of-place batch repair), and used by later calls in that bucket.
+ *   out   scratch output of the same size as in (written).
+ *   best  (optional, host) receives the chosen configuration.
+ */
+int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t n, int reps, utf16_config *best);
+int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t num_strings, int reps,
+                         utf16_config *best);
+
+/*
+ * UTF16_ETIMEOUT if a kernel of this device gave up a bounded wait (a TMA
+ * copy that did not complete within one second) since the last call, which
+ * means its outputs are not valid; UTF16_OK otherwise.  Synchronises the
+ * device.
+ */
+int utf16_check_device_errors(void);
+
+/*
  * Prepare the current device (SM count, occupancy, scratch pool, launch
  * tuning).  Called implicitly by the first entry point that needs it; call it
  * explicitly before capturing a stream into a CUDA graph, since it allocates.

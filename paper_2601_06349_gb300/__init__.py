@@ -31,6 +31,19 @@ class Utf16Error(RuntimeError):
         super().__init__(f"{where}: {strerror(code)} (status {code})")
 
 
+class Config(ctypes.Structure):
+    """Launch configuration (utf16_config in include/utf16wf.h)."""
+    _fields_ = [("single_variant", ctypes.c_int), ("single_units_per_thread", ctypes.c_int),
+                ("single_blocks_per_sm", ctypes.c_int), ("batch_units_per_thread", ctypes.c_int),
+                ("batch_prefetch", ctypes.c_int), ("batch_blocks_per_sm", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+VARIANT_LDG, VARIANT_LDG_PREFETCH, VARIANT_TMA = 0, 1, 2
+
+
 def _declare(lib):
     c_u16p = ctypes.c_void_p
     i64 = ctypes.c_int64
@@ -46,6 +59,12 @@ def _declare(lib):
         "utf16_is_well_formed_batch": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "utf16_to_well_formed_host": ([c_u16p, c_u16p, i64, vp], ctypes.c_int),
         "utf16_init_device": ([], ctypes.c_int),
+        "utf16_get_config": ([ctypes.POINTER(Config)], ctypes.c_int),
+        "utf16_set_config": ([ctypes.POINTER(Config)], ctypes.c_int),
+        "utf16_autotune_single": ([vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
+        "utf16_autotune_batch": ([vp, vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
+        "utf16_check_device_errors": ([], ctypes.c_int),
+        "utf16_to_well_formed_first_bad_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "utf16_release_device": ([], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -249,3 +268,53 @@ def init_device():
 
 def release_device():
     _check(lib().utf16_release_device(), "utf16_release_device")
+
+
+def get_config() -> Config:
+    c = Config()
+    _check(lib().utf16_get_config(ctypes.byref(c)), "utf16_get_config")
+    return c
+
+
+def set_config(cfg: Config | None = None, **fields) -> Config:
+    """Set the current device's default launch configuration (clears tuned
+    entries).  Fields not given keep their current value."""
+    c = get_config() if cfg is None else cfg
+    for k, v in fields.items():
+        setattr(c, k, int(v))
+    _check(lib().utf16_set_config(ctypes.byref(c)), "utf16_set_config")
+    return c
+
+
+def autotune_single(inp, out=None, reps: int = 5) -> Config:
+    """Time every configuration on this string (out-of-place repair with the
+    first-error index) and keep the fastest for its size bucket."""
+    torch = _torch()
+    _units(inp, "inp")
+    if out is None:
+        out = torch.empty_like(inp)
+    best = Config()
+    with torch.cuda.device(inp.device):
+        _check(lib().utf16_autotune_single(inp.data_ptr(), out.data_ptr(), inp.numel(), reps, ctypes.byref(best)),
+               "utf16_autotune_single")
+    return best
+
+
+def autotune_batch(units, offsets, out=None, reps: int = 5) -> Config:
+    """Time every batch configuration on this batch and keep the fastest for
+    its bucket of string count."""
+    torch = _torch()
+    _units(units)
+    _offsets(offsets)
+    if out is None:
+        out = torch.empty_like(units)
+    best = Config()
+    with torch.cuda.device(units.device):
+        _check(lib().utf16_autotune_batch(units.data_ptr(), out.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
+                                          reps, ctypes.byref(best)), "utf16_autotune_batch")
+    return best
+
+
+def check_device_errors():
+    """Raise if a kernel gave up a bounded wait since the last check."""
+    _check(lib().utf16_check_device_errors(), "utf16_check_device_errors")

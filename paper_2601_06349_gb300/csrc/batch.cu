@@ -62,146 +62,129 @@ __device__ __forceinline__ long long lower_bound_warp(const long long *offsets, 
     return lo;
 }
 
-template <int MODE, int ST, int U>
-__global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A) {
+template <int MODE, int U>
+__device__ __forceinline__ void load_batch_chunk(const BatchArgs &A, const uint4 *vin, long long vfirst, long long lo,
+                                                 long long hi, int lane, uint4 (&v)[U]) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
-    constexpr int kWords = (int)(CU / 32) + 1;  // bit CU marks a start just past the chunk
-    __shared__ uint32_t s_bits[kBlockThreads / 32][kWords];
-
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    uint32_t *bits = s_bits[wib];
-
-    const long long lo = A.offsets[0];
-    const long long hi = A.offsets[A.count];
-    if (lo < 0 || hi <= lo) return;
-    const long long vbeg = (lo + A.a) >> 3;
-    const long long vend = (hi + A.a + 7) >> 3;
-    const long long chunks = (vend - vbeg + 32LL * U - 1) / (32LL * U);
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long c_begin = gwarp * chunks / nwarps;
-    const long long c_end = (gwarp + 1) * chunks / nwarps;
-    const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
-
-    long long hint = 0;
-    for (long long c = c_begin; c < c_end; ++c) {
-        const long long vfirst = vbeg + c * (32LL * U);
-        const long long cfirst = vfirst * 8 - A.a;
-        const bool edge = (cfirst < lo) || (cfirst + CU > hi);
-        uint4 v[U];
-        uint32_t valid = 0xFFFFFFFFu;
-        if (!edge) {
-            const uint4 *p = vin + vfirst + lane;
+    const long long cfirst = vfirst * 8 - A.a;
+    if (cfirst >= lo && cfirst + CU <= hi) {
+        const uint4 *p = vin + vfirst + lane;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if constexpr (MODE == kModeInPlace)
-                    v[u] = ld_plain(p + 32 * u);
-                else
-                    v[u] = ld_stream(p + 32 * u);
+        for (int u = 0; u < U; ++u) {
+            if constexpr (MODE == kModeInPlace)
+                v[u] = ld_plain(p + 32 * u);
+            else
+                v[u] = ld_stream(p + 32 * u);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
+            v[u] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const long long p = p0 + k;
+                if (p >= lo && p < hi) vec_set_unit(v[u], k, A.in[p]);
             }
-        } else {
-            valid = 0;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t batch_valid_bits8(long long p0, long long lo, long long hi) {
+    const long long a = lo - p0 > 0 ? lo - p0 : 0;
+    const long long b = hi - p0 < 8 ? hi - p0 : 8;
+    if (b <= a) return 0u;
+    return ((1u << b) - 1u) & ~((1u << a) - 1u);
+}
+
+template <int MODE, int ST, int U>
+__device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long long cfirst, long long lo, long long hi,
+                                                    const uint4 (&v)[U], int lane, uint32_t *bits, long long &hint) {
+    constexpr long long CU = (long long)U * kWarpSliceUnits;
+    constexpr int kWords = (int)(CU / 32) + 1;
+    const bool edge = (cfirst < lo) || (cfirst + CU > hi);
+    const uint32_t surr = any_surrogate<U>(v);
+
+    if (!__any_sync(kFull, surr != 0)) {
+        if constexpr (MODE == kModeOut) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
-                v[u] = make_uint4(0, 0, 0, 0);
+                if (!edge) {
+                    store_vec<ST>(A.out + p0, v[u]);
+                } else {
+                    const uint32_t w8 = batch_valid_bits8(p0, lo, hi);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const long long p = p0 + k;
-                    if (p >= lo && p < hi) {
-                        vec_set_unit(v[u], k, A.in[p]);
-                        valid |= 1u << (8 * u + k);
-                    }
+                    for (int k = 0; k < 8; ++k)
+                        if (w8 & (1u << k)) A.out[p0 + k] = (uint16_t)vec_unit(v[u], k);
                 }
             }
         }
-        if constexpr (U < 4) valid &= (1u << (8 * U)) - 1u;
+        return;
+    }
 
-        uint32_t surr = 0;
+    // String starts in [cfirst, cfirst + CU].
+    for (int i = lane; i < kWords; i += 32) bits[i] = 0u;
+    __syncwarp();
+    const long long s_first = lower_bound_warp(A.offsets, A.count, hint, cfirst, lane);
+    hint = s_first;
+    long long s_last = s_first - 1;  // last string index starting in the chunk
+    for (long long base = s_first;; base += 32) {
+        const long long idx = base + lane;
+        const long long off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
+        const bool inside = off >= cfirst && off <= cfirst + CU;
+        if (inside) {
+            const long long r = off - cfirst;
+            atomicOr(&bits[r >> 5], 1u << (r & 31));
+        }
+        const unsigned m = __ballot_sync(kFull, inside);
+        s_last = base + __popc(m) - 1 > s_last ? base + __popc(m) - 1 : s_last;
+        if (m != kFull) break;
+    }
+    __syncwarp();
+    uint32_t hp = 0, hn = 0;
+    if (lane == 0) {
+        const long long p = cfirst - 1;
+        hp = (p >= lo && p < hi) ? unit_is_high(A.in[p]) : 0u;
+    }
+    if (lane == 31) {
+        const long long p = cfirst + CU;
+        hn = (p >= lo && p < hi) ? unit_is_low(A.in[p]) : 0u;
+    }
+    uint32_t from_prev, from_next;
+    neighbour_bits<U>(v, hp, hn, lane, from_prev, from_next);
+    long long prev_s = -1;
+    const long long s_lo = hint > 0 ? hint - 1 : 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u) surr |= any_surrogate(v[u]);
-
-        if (!__any_sync(kFull, surr != 0)) {
-            if constexpr (MODE == kModeOut) {
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
-                    if (!edge) {
-                        store_vec<ST>(A.out + p0, v[u]);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            if (valid & (1u << (8 * u + k))) A.out[p0 + k] = (uint16_t)vec_unit(v[u], k);
-                    }
-                }
-            }
-            continue;
+    for (int u = 0; u < U; ++u) {
+        const int r0 = u * kWarpSliceUnits + lane * kUnitsPerVec;
+        const long long p0 = cfirst + r0;
+        const unsigned long long w2 =
+            (unsigned long long)bits[r0 >> 5] | ((unsigned long long)bits[(r0 >> 5) + 1] << 32);
+        const uint32_t s9 = (uint32_t)(w2 >> (r0 & 31)) & 0x1FFu;  // string starts at units r0 .. r0+8
+        uint32_t st_lo, st_hi;
+        bits_to_flags(s9 & 0xFFu, st_lo, st_hi);
+        uint32_t bad_lo, bad_hi;
+        vec_mismatch(v[u], (from_prev >> u) & 1u, (from_next >> u) & 1u, st_lo, st_hi, (s9 >> 8) & 1u, bad_lo,
+                     bad_hi);
+        if (edge) {
+            uint32_t vlo, vhi;
+            bits_to_flags(batch_valid_bits8(p0, lo, hi), vlo, vhi);
+            bad_lo &= vlo;
+            bad_hi &= vhi;
         }
-
-        // String starts in [cfirst, cfirst + CU].
-        for (int i = lane; i < kWords; i += 32) bits[i] = 0u;
-        __syncwarp();
-        const long long s_first = lower_bound_warp(A.offsets, A.count, hint, cfirst, lane);
-        hint = s_first;
-        long long s_last = s_first - 1;  // last string index starting in the chunk
-        for (long long base = s_first;; base += 32) {
-            const long long idx = base + lane;
-            const long long off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
-            const bool inside = off >= cfirst && off <= cfirst + CU;
-            if (inside) {
-                const long long r = off - cfirst;
-                atomicOr(&bits[r >> 5], 1u << (r & 31));
-            }
-            const unsigned m = __ballot_sync(kFull, inside);
-            s_last = base + __popc(m) - 1 > s_last ? base + __popc(m) - 1 : s_last;
-            if (m != kFull) break;
-        }
-        __syncwarp();
-        uint32_t no_prev = 0, no_next = 0;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int r0 = u * kWarpSliceUnits + lane * kUnitsPerVec;
-            const unsigned long long w2 =
-                (unsigned long long)bits[r0 >> 5] | ((unsigned long long)bits[(r0 >> 5) + 1] << 32);
-            const uint32_t s9 = (uint32_t)(w2 >> (r0 & 31)) & 0x1FFu;  // starts at units r0 .. r0+8
-            no_prev |= (s9 & 0xFFu) << (8 * u);
-            no_next |= ((s9 >> 1) & 0xFFu) << (8 * u);
-        }
-
-        uint32_t h = 0, l = 0;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            uint32_t hu, lu;
-            classify8(v[u], hu, lu);
-            h |= hu << (8 * u);
-            l |= lu << (8 * u);
-        }
-        uint32_t halo_prev = 0, halo_next = 0;
-        if (lane == 0) {
-            const long long p = cfirst - 1;
-            halo_prev = (p >= lo && p < hi) ? unit_is_high(A.in[p]) : 0u;
-        }
-        if (lane == 31) {
-            const long long p = cfirst + CU;
-            halo_next = (p >= lo && p < hi) ? unit_is_low(A.in[p]) : 0u;
-        }
-        const uint32_t bad = mismatch_mask<U>(h, l, halo_prev, halo_next, no_prev, no_next, lane) & valid;
-
+        const bool vb = (bad_lo | bad_hi) != 0;
         if constexpr (MODE != kModeCheck) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t b8 = (bad >> (8 * u)) & 0xFFu;
-                if (MODE == kModeInPlace && b8 == 0) continue;
-                const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
-                const uint4 f = fix_vec(v[u], b8);
+            if (MODE == kModeOut || vb) {
+                const uint4 f = vb ? fix_vec(v[u], bad_lo, bad_hi) : v[u];
                 if (!edge) {
                     if constexpr (MODE == kModeInPlace)
                         *reinterpret_cast<uint4 *>(A.out + p0) = f;
                     else
                         store_vec<ST>(A.out + p0, f);
                 } else {
-                    const uint32_t w8 = (MODE == kModeInPlace) ? b8 : ((valid >> (8 * u)) & 0xFFu);
+                    const uint32_t w8 = (MODE == kModeInPlace) ? (gather4(bad_lo) | (gather4(bad_hi) << 4))
+                                                               : batch_valid_bits8(p0, lo, hi);
 #pragma unroll
                     for (int k = 0; k < 8; ++k)
                         if (w8 & (1u << k)) A.out[p0 + k] = (uint16_t)vec_unit(f, k);
@@ -210,13 +193,11 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
         } else {
             // Per-string first-error index: the first bad unit of each string
             // within this thread's units, one atomic per (thread, string).
-            uint32_t rest = bad;
-            long long prev_s = -1;
-            const long long s_lo = hint > 0 ? hint - 1 : 0;
+            uint32_t rest = gather4(bad_lo) | (gather4(bad_hi) << 4);
             while (rest) {
                 const int b = __ffs(rest) - 1;
                 rest &= rest - 1;
-                const long long p = cfirst + (b >> 3) * kWarpSliceUnits + lane * kUnitsPerVec + (b & 7);
+                const long long p = p0 + b;
                 long long a_i = s_lo, b_i = s_last > s_lo ? s_last : s_lo;
                 while (a_i < b_i) {  // largest index with offsets[index] <= p
                     const long long mid = (a_i + b_i + 1) >> 1;
@@ -235,6 +216,48 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
     }
 }
 
+template <int MODE, int ST, int U, bool PF>
+__global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A) {
+    constexpr int kWords = U * kWarpSliceUnits / 32 + 1;  // bit CU marks a start just past the chunk
+    __shared__ uint32_t s_bits[kBlockThreads / 32][kWords];
+
+    const int lane = threadIdx.x & 31;
+    uint32_t *bits = s_bits[threadIdx.x >> 5];
+
+    const long long lo = A.offsets[0];
+    const long long hi = A.offsets[A.count];
+    if (lo < 0 || hi <= lo) return;
+    const long long vbeg = (lo + A.a) >> 3;
+    const long long vend = (hi + A.a + 7) >> 3;
+    const long long chunks = (vend - vbeg + 32LL * U - 1) / (32LL * U);
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long c_begin = gwarp * chunks / nwarps;
+    const long long c_end = (gwarp + 1) * chunks / nwarps;
+    const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
+
+    long long hint = 0;
+    if constexpr (PF) {
+        uint4 nv[U];
+        if (c_begin < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + c_begin * (32LL * U), lo, hi, lane, nv);
+        for (long long c = c_begin; c < c_end; ++c) {
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = nv[u];
+            if (c + 1 < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + (c + 1) * (32LL * U), lo, hi, lane, nv);
+            const long long cfirst = (vbeg + c * (32LL * U)) * 8 - A.a;
+            process_batch_chunk<MODE, ST, U>(A, cfirst, lo, hi, v, lane, bits, hint);
+        }
+    } else {
+        for (long long c = c_begin; c < c_end; ++c) {
+            const long long vfirst = vbeg + c * (32LL * U);
+            uint4 v[U];
+            load_batch_chunk<MODE, U>(A, vin, vfirst, lo, hi, lane, v);
+            process_batch_chunk<MODE, ST, U>(A, vfirst * 8 - A.a, lo, hi, v, lane, bits, hint);
+        }
+    }
+}
+
 // first_bad[s] = length of string s (the value for a well-formed string).
 __global__ void batch_lengths_kernel(const long long *offsets, long long count, long long *first_bad) {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -243,22 +266,19 @@ __global__ void batch_lengths_kernel(const long long *offsets, long long count, 
 }
 
 template <int MODE, int ST>
-static const void *batch_ptr(int u) {
-    switch (u) {
-        case 1: return (const void *)batch_kernel<MODE, ST, 1>;
-        case 2: return (const void *)batch_kernel<MODE, ST, 2>;
-        default: return (const void *)batch_kernel<MODE, ST, 4>;
-    }
+static const void *batch_ptr(int u, bool pf) {
+    if (pf) return u == 2 ? (const void *)batch_kernel<MODE, ST, 2, true> : (const void *)batch_kernel<MODE, ST, 4, true>;
+    return u == 2 ? (const void *)batch_kernel<MODE, ST, 2, false> : (const void *)batch_kernel<MODE, ST, 4, false>;
 }
 
-static const void *pick_batch(int mode, int st, int u) {
-    if (mode == kModeCheck) return batch_ptr<kModeCheck, 16>(u);
-    if (mode == kModeInPlace) return batch_ptr<kModeInPlace, 16>(u);
+static const void *pick_batch(int mode, int st, int u, bool pf) {
+    if (mode == kModeCheck) return batch_ptr<kModeCheck, 16>(u, pf);
+    if (mode == kModeInPlace) return batch_ptr<kModeInPlace, 16>(u, pf);
     switch (st) {
-        case 16: return batch_ptr<kModeOut, 16>(u);
-        case 8: return batch_ptr<kModeOut, 8>(u);
-        case 4: return batch_ptr<kModeOut, 4>(u);
-        default: return batch_ptr<kModeOut, 2>(u);
+        case 16: return batch_ptr<kModeOut, 16>(u, pf);
+        case 8: return batch_ptr<kModeOut, 8>(u, pf);
+        case 4: return batch_ptr<kModeOut, 4>(u, pf);
+        default: return batch_ptr<kModeOut, 2>(u, pf);
     }
 }
 
@@ -283,12 +303,14 @@ cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    const void *fn = pick_batch(L.mode, st, L.units_per_thread);
+    const void *fn = pick_batch(L.mode, st, L.units_per_thread == 2 ? 2 : 4, L.prefetch);
     void *args[] = {(void *)&A};
     return cudaLaunchKernel(fn, dim3((unsigned)L.blocks), dim3(kBlockThreads), args, 0, stream);
 }
 
-const void *batch_kernel_for_occupancy(int mode, int u) { return pick_batch(mode, 16, u); }
+const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch) {
+    return pick_batch(mode, 16, u == 2 ? 2 : 4, prefetch);
+}
 
 // ---------------------------------------------------------------------------
 __global__ void init_slots_kernel(Slot *slots, int count) {

@@ -2,14 +2,19 @@
 //
 // A thread owns runs of 8 code units held in one 16-byte vector (uint4).  A
 // warp covers 32 consecutive vectors (512 bytes) per "slice"; a warp "chunk"
-// is U consecutive slices.  Per thread, the units of its U vectors are
-// described by 32-bit masks with bit 8*u + k for unit k of slice u (U <= 4).
+// is U consecutive slices (U <= 4).
 //
 // Classification follows Section 3.1 of the paper (mask with 0xFC00, compare
 // with 0xD800 / 0xDC00), applied to the high byte only as in the paper's NEON
 // variant (Section 3.3: the more significant byte decides high / low /
-// neither): byte & 0xFC == 0xD8 is high, == 0xDC is low, byte & 0xF8 == 0xD8
-// is any surrogate.
+// neither).  The 8 high bytes of a vector are gathered into two 32-bit words
+// (units 0..3 and 4..7) and every per-unit property is kept as a "byte-lane
+// flag": bit 8k+7 of the word is set when unit k has the property.  Then
+//   surrogate  : high byte & 0xF8 == 0xD8   (exact zero-byte test)
+//   low        : surrogate and bit 2 of the high byte set (0xDC..0xDF)
+//   high       : surrogate and bit 2 clear   (0xD8..0xDB)
+// and the neighbours of Section 3.1's step three are 8-bit funnel shifts of
+// these words: flag of unit k-1 at bit 8k+7, flag of unit k+1 at bit 8k+7.
 #pragma once
 
 #include <stdint.h>
@@ -19,7 +24,7 @@ namespace u16wf {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kUnitsPerVec = 8;
 constexpr int kWarpSliceUnits = 32 * kUnitsPerVec;  // 256 units = 512 bytes
-constexpr uint16_t kReplacement = 0xFFFD;
+constexpr uint32_t kFlagBits = 0x80808080u;
 
 // Scratch slot used by first-error reductions (one per stream).  `min` holds
 // the smallest bad index seen so far (all ones = none), `done` counts
@@ -33,57 +38,56 @@ struct Slot {
 };
 static_assert(sizeof(Slot) == 32, "slot size");
 
-// High bytes of the 8 units of v: units 0..3 in b03, 4..7 in b47.
-__device__ __forceinline__ void high_bytes(const uint4 &v, uint32_t &b03, uint32_t &b47) {
-    b03 = __byte_perm(v.x, v.y, 0x7531);
-    b47 = __byte_perm(v.z, v.w, 0x7531);
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+    return r;
 }
 
-// Nonzero iff some unit of v is a surrogate.  (x - 0x01..) & ~x & 0x80..
-// is nonzero exactly when x has a zero byte.
-__device__ __forceinline__ uint32_t any_surrogate(const uint4 &v) {
-    uint32_t b03, b47;
-    high_bytes(v, b03, b47);
-    const uint32_t x0 = (b03 & 0xF8F8F8F8u) ^ 0xD8D8D8D8u;
-    const uint32_t x1 = (b47 & 0xF8F8F8F8u) ^ 0xD8D8D8D8u;
-    return ((x0 - 0x01010101u) & ~x0 & 0x80808080u) | ((x1 - 0x01010101u) & ~x1 & 0x80808080u);
+// High bytes of the 8 units of v: units 0..3 in `lo`, 4..7 in `hi`.
+__device__ __forceinline__ void high_bytes(const uint4 &v, uint32_t &lo, uint32_t &hi) {
+    lo = prmt(v.x, v.y, 0x7531);
+    hi = prmt(v.z, v.w, 0x7531);
 }
 
-// 4-bit mask, bit k set iff byte k of x is zero (exact per byte: no borrow
-// crosses bytes because the low seven bits plus 0x7F stay below 0x100).
-__device__ __forceinline__ uint32_t zero_bytes4(uint32_t x) {
-    const uint32_t nonzero = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
-    const uint32_t z = (~nonzero & 0x80808080u) >> 7;  // bits 0, 8, 16, 24
-    return ((z * 0x00204081u) >> 21) & 0xFu;          // gathers them to bits 0..3
+// Bit 8k+7 set iff byte k of x is zero.  Exact per byte: the low seven bits
+// plus 0x7F never carry out of the byte.
+__device__ __forceinline__ uint32_t zero_byte_flags(uint32_t x) {
+    return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & kFlagBits;
 }
 
-// 8-bit masks (bit k = unit k) of high and low surrogates in v.
-__device__ __forceinline__ void classify8(const uint4 &v, uint32_t &h, uint32_t &l) {
-    uint32_t b03, b47;
-    high_bytes(v, b03, b47);
-    const uint32_t m03 = b03 & 0xFCFCFCFCu, m47 = b47 & 0xFCFCFCFCu;
-    h = zero_bytes4(m03 ^ 0xD8D8D8D8u) | (zero_bytes4(m47 ^ 0xD8D8D8D8u) << 4);
-    l = zero_bytes4(m03 ^ 0xDCDCDCDCu) | (zero_bytes4(m47 ^ 0xDCDCDCDCu) << 4);
+__device__ __forceinline__ uint32_t surrogate_flags(uint32_t hb) {
+    return zero_byte_flags((hb & 0xF8F8F8F8u) ^ 0xD8D8D8D8u);
 }
 
-__device__ __forceinline__ bool unit_is_high(uint32_t u) { return (u & 0xFC00u) == 0xD800u; }
-__device__ __forceinline__ bool unit_is_low(uint32_t u) { return (u & 0xFC00u) == 0xDC00u; }
+// Bit 2 of every high byte moved to bit 7: set for 0xDC..0xDF among surrogates.
+__device__ __forceinline__ uint32_t low_half_flags(uint32_t hb) { return (hb << 5) & kFlagBits; }
 
-// Bit u (u < 4) moved to bit 8*u.
+// Bit u (u < 4) moved to bit 8u.
 __device__ __forceinline__ uint32_t spread4(uint32_t x) { return (x * 0x00204081u) & 0x01010101u; }
 
-// Replace the units of a 32-bit word (2 units) flagged in bad2 (bits 0, 1).
-__device__ __forceinline__ uint32_t fix_word(uint32_t w, uint32_t bad2) {
-    const uint32_t m = ((bad2 & 1u) ? 0x0000FFFFu : 0u) | ((bad2 & 2u) ? 0xFFFF0000u : 0u);
-    return (w & ~m) | (0xFFFDFFFDu & m);
+// Bits 8k+7 (k < 4) gathered to bits 0..3.
+__device__ __forceinline__ uint32_t gather4(uint32_t flags) { return (((flags >> 7) * 0x00204081u) >> 21) & 0xFu; }
+
+// Replace by U+FFFD every unit whose byte-lane flag is set (lo: units 0..3,
+// hi: units 4..7).  prmt with a selector nibble 8+k replicates the sign bit
+// of byte k, so each unit gets an all-ones or all-zeros 16-bit mask.
+__device__ __forceinline__ uint4 fix_vec(uint4 v, uint32_t bad_lo, uint32_t bad_hi) {
+    uint32_t m;
+    m = prmt(bad_lo, 0u, 0x9988);
+    v.x = (v.x & ~m) | (0xFFFDFFFDu & m);
+    m = prmt(bad_lo, 0u, 0xBBAA);
+    v.y = (v.y & ~m) | (0xFFFDFFFDu & m);
+    m = prmt(bad_hi, 0u, 0x9988);
+    v.z = (v.z & ~m) | (0xFFFDFFFDu & m);
+    m = prmt(bad_hi, 0u, 0xBBAA);
+    v.w = (v.w & ~m) | (0xFFFDFFFDu & m);
+    return v;
 }
 
-__device__ __forceinline__ uint4 fix_vec(uint4 v, uint32_t bad8) {
-    v.x = fix_word(v.x, bad8);
-    v.y = fix_word(v.y, bad8 >> 2);
-    v.z = fix_word(v.z, bad8 >> 4);
-    v.w = fix_word(v.w, bad8 >> 6);
-    return v;
+// Index (0..7) of the first flagged unit; requires bad_lo | bad_hi != 0.
+__device__ __forceinline__ int first_flag(uint32_t bad_lo, uint32_t bad_hi) {
+    return bad_lo ? ((__ffs(bad_lo) - 1) >> 3) : 4 + ((__ffs(bad_hi) - 1) >> 3);
 }
 
 __device__ __forceinline__ uint32_t vec_unit(const uint4 &v, int k) {
@@ -96,36 +100,75 @@ __device__ __forceinline__ void vec_set_unit(uint4 &v, int k, uint32_t u) {
     *w = (k & 1) ? ((*w & 0x0000FFFFu) | (u << 16)) : ((*w & 0xFFFF0000u) | u);
 }
 
-// Mismatch mask for a warp chunk of U slices (Section 1 rule).
-//   h, l       this lane's high / low masks (bit 8u+k)
-//   halo_prev  1 if the unit just before the chunk is a high surrogate that
-//              may pair with the chunk's first unit (only lane 0's value is used)
-//   halo_next  1 if the unit just after the chunk is a low surrogate that may
-//              pair with the chunk's last unit (only lane 31's value is used)
-//   no_prev    bit 8u+k set: unit k of slice u has no left neighbour (string start)
-//   no_next    bit 8u+k set: unit k of slice u has no right neighbour (string end)
-// A unit's left neighbour is the previous unit of the same vector, the last
-// unit of the previous lane's vector, or (lane 0) the last unit of lane 31's
-// vector in the previous slice; symmetrically on the right.
+__device__ __forceinline__ bool unit_is_high(uint32_t u) { return (u & 0xFC00u) == 0xD800u; }
+__device__ __forceinline__ bool unit_is_low(uint32_t u) { return (u & 0xFC00u) == 0xDC00u; }
+
+// Byte-lane flags of 8 per-unit bits (bit k = unit k).
+__device__ __forceinline__ void bits_to_flags(uint32_t bits8, uint32_t &lo, uint32_t &hi) {
+    lo = spread4(bits8 & 0xFu) << 7;
+    hi = spread4((bits8 >> 4) & 0xFu) << 7;
+}
+
+// Nonzero iff some unit of the U vectors is a surrogate.
 template <int U>
-__device__ __forceinline__ uint32_t mismatch_mask(uint32_t h, uint32_t l, uint32_t halo_prev, uint32_t halo_next,
-                                                  uint32_t no_prev, uint32_t no_next, int lane) {
-    static_assert(U >= 1 && U <= 4, "masks hold at most 4 slices");
-    constexpr uint32_t kSliceMask = (U == 4) ? 0xFFFFFFFFu : ((1u << (8 * U)) - 1u);
+__device__ __forceinline__ uint32_t any_surrogate(const uint4 (&v)[U]) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        uint32_t lo, hi;
+        high_bytes(v[u], lo, hi);
+        // (x - 0x01..) & ~x & 0x80.. is nonzero exactly when x has a zero byte.
+        const uint32_t x0 = (lo & 0xF8F8F8F8u) ^ 0xD8D8D8D8u;
+        const uint32_t x1 = (hi & 0xF8F8F8F8u) ^ 0xD8D8D8D8u;
+        acc |= ((x0 - 0x01010101u) & ~x0) | ((x1 - 0x01010101u) & ~x1);
+    }
+    return acc & kFlagBits;
+}
+
+// Cross-lane neighbour bits of a warp chunk: bit u of `from_prev` is set when
+// the unit just before this lane's vector u is a high surrogate, bit u of
+// `from_next` when the unit just after it is a low surrogate.  That unit is
+// the last (first) unit of the adjacent lane's vector, or for lane 0 (31) the
+// last unit of lane 31's vector in the previous slice (lane 0's in the next
+// slice), or the halo unit just outside the chunk:
+//   halo_prev   lane 0: the unit before the chunk is a high surrogate
+//   halo_next   lane 31: the unit after the chunk is a low surrogate
+template <int U>
+__device__ __forceinline__ void neighbour_bits(const uint4 (&v)[U], uint32_t halo_prev, uint32_t halo_next, int lane,
+                                               uint32_t &from_prev, uint32_t &from_next) {
     uint32_t last_h = 0, first_l = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        last_h |= ((h >> (8 * u + 7)) & 1u) << u;
-        first_l |= ((l >> (8 * u)) & 1u) << u;
+        last_h |= (uint32_t)unit_is_high(v[u].w >> 16) << u;
+        first_l |= (uint32_t)unit_is_low(v[u].x & 0xFFFFu) << u;
     }
-    uint32_t from_prev = __shfl_sync(kFull, last_h, (lane + 31) & 31);
-    uint32_t from_next = __shfl_sync(kFull, first_l, (lane + 1) & 31);
-    if (lane == 0) from_prev = ((from_prev << 1) | (halo_prev & 1u)) & ((1u << U) - 1u);
+    from_prev = __shfl_sync(kFull, last_h, (lane + 31) & 31);
+    from_next = __shfl_sync(kFull, first_l, (lane + 1) & 31);
+    if (lane == 0) from_prev = (from_prev << 1) | (halo_prev & 1u);
     if (lane == 31) from_next = (from_next >> 1) | ((halo_next & 1u) << (U - 1));
-    // bit 8u+k: unit k-1 (or the neighbour) is high / unit k+1 (or the neighbour) is low
-    const uint32_t prev_is_high = (((h << 1) & ~0x01010101u) | spread4(from_prev)) & ~no_prev & kSliceMask;
-    const uint32_t next_is_low = (((l >> 1) & ~0x80808080u) | (spread4(from_next) << 7)) & ~no_next & kSliceMask;
-    return ((h & ~next_is_low) | (l & ~prev_is_high)) & kSliceMask;
+}
+
+// Mismatch flags of one vector (Section 1 rule, Section 3.1 step three).
+//   prev_h   1 if the unit before the vector is a high surrogate
+//   next_l   1 if the unit after the vector is a low surrogate
+//   st_lo/hi byte-lane flags of units that start a string (no left
+//            neighbour); st_next: the unit after the vector starts one.
+//            All zero for a single string.
+__device__ __forceinline__ void vec_mismatch(const uint4 &v, uint32_t prev_h, uint32_t next_l, uint32_t st_lo,
+                                             uint32_t st_hi, uint32_t st_next, uint32_t &bad_lo, uint32_t &bad_hi) {
+    uint32_t lo, hi;
+    high_bytes(v, lo, hi);
+    const uint32_t s_lo = surrogate_flags(lo), s_hi = surrogate_flags(hi);
+    const uint32_t b_lo = low_half_flags(lo), b_hi = low_half_flags(hi);
+    const uint32_t h_lo = s_lo & ~b_lo, h_hi = s_hi & ~b_hi;
+    const uint32_t l_lo = s_lo & b_lo, l_hi = s_hi & b_hi;
+    // flag of unit k-1 / unit k+1 at bit 8k+7
+    const uint32_t ph_lo = __funnelshift_l(prev_h << 31, h_lo, 8) & ~st_lo;
+    const uint32_t ph_hi = __funnelshift_l(h_lo, h_hi, 8) & ~st_hi;
+    const uint32_t nl_lo = __funnelshift_r(l_lo, l_hi, 8) & ~__funnelshift_r(st_lo, st_hi, 8);
+    const uint32_t nl_hi = __funnelshift_r(l_hi, next_l << 7, 8) & ~__funnelshift_r(st_hi, st_next << 7, 8);
+    bad_lo = (h_lo & ~nl_lo) | (l_lo & ~ph_lo);
+    bad_hi = (h_hi & ~nl_hi) | (l_hi & ~ph_hi);
 }
 
 // Warp-wide minimum of a 64-bit value.
@@ -138,20 +181,17 @@ __device__ __forceinline__ long long warp_min_ll(long long v) {
     return v;
 }
 
-// Streaming 16-byte loads / stores.
+// 16-byte loads / stores.
 __device__ __forceinline__ uint4 ld_stream(const uint4 *p) { return __ldcs(p); }
-__device__ __forceinline__ uint4 ld_nc(const uint4 *p) { return __ldg(p); }
 __device__ __forceinline__ uint4 ld_plain(const uint4 *p) {
     uint4 v;
-    asm volatile("ld.global.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
+    asm volatile("ld.global.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
     return v;
 }
 __device__ __forceinline__ void st_stream(uint4 *p, const uint4 &v) { __stcs(p, v); }
 
-// Store the 8 units of v at out + p0, where out + p0 has the alignment
-// implied by ST (16, 8, 4 bytes, or 2 = odd unit index relative to 4 bytes).
+// Store the 8 units of v at dst, whose alignment is implied by ST (16, 8 or
+// 4 bytes, or 2 = an odd unit index relative to 4 bytes).
 template <int ST>
 __device__ __forceinline__ void store_vec(uint16_t *dst, const uint4 &v) {
     if constexpr (ST == 16) {

@@ -121,7 +121,6 @@ extern "C" int utf16_to_well_formed_host(const uint16_t *host_in, uint16_t *host
         rc = ctx->slot_for(ctx->lanes[i], &slots[i]);
         if (rc) return rc;
     }
-    const int blocks = ctx->blocks_for(single_kernel_for_occupancy(kModeInPlace, true, ctx->single_u));
     for (int64_t k = 0; k < chunks; ++k) {
         const int lane = (int)(k % kHostLanes);
         cudaStream_t s = ctx->lanes[lane];
@@ -136,8 +135,7 @@ extern "C" int utf16_to_well_formed_host(const uint16_t *host_in, uint16_t *host
             L.n = len;
             L.mode = kModeInPlace;
             L.first_bad = true;
-            L.units_per_thread = ctx->single_u;
-            L.max_blocks = blocks;
+            configure_single(ctx, ctx->single_config(len), L);
             L.slot = slots[lane];
             L.result = &slots[lane]->result;
             L.lead = lead[(size_t)k];

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace u16wf {
@@ -17,35 +18,47 @@ enum Mode : int {
     kModeCheck = 2,    // read-only first-error index
 };
 
+// How the single-string kernels bring data in.
+enum Variant : int {
+    kVariantLdg = 0,          // 128-bit loads, one chunk at a time
+    kVariantLdgPrefetch = 1,  // 128-bit loads, next chunk requested before this one is processed
+    kVariantTma = 2,          // bulk copies (TMA) into a 4-stage shared-memory ring
+};
+
 struct SingleLaunch {
-    const uint16_t *in;
-    uint16_t *out;
-    long long n;
-    int mode;
-    bool first_bad;
-    int units_per_thread;  // U: 16-byte vectors per thread per chunk (1, 2 or 4)
-    int max_blocks;        // persistent grid cap (SMs x resident blocks)
-    Slot *slot;
-    long long *result;
-    uint32_t lead, trail;  // outside neighbours (0 = none)
+    const uint16_t *in = nullptr;
+    uint16_t *out = nullptr;
+    long long n = 0;
+    int mode = kModeOut;
+    bool first_bad = false;
+    int units_per_thread = 4;  // U: 16-byte vectors per thread per chunk (2 or 4; TMA uses 4)
+    int variant = kVariantLdg;
+    int max_blocks = 1;        // persistent grid cap (SMs x resident blocks)
+    Slot *slot = nullptr;
+    long long *result = nullptr;
+    uint32_t lead = 0, trail = 0;  // outside neighbours (0 = none)
 };
 
 cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream);
-const void *single_kernel_for_occupancy(int mode, bool fb, int u);
+const void *single_kernel_for_occupancy(int mode, bool fb, int u, int variant = kVariantLdg);
+size_t single_tma_smem_bytes();
+cudaError_t prepare_single_tma();
+unsigned int read_and_clear_tma_timeout();
 
 struct BatchLaunch {
-    const uint16_t *in;
-    uint16_t *out;
-    const long long *offsets;
-    long long count;
-    long long *first_bad;  // kModeCheck only
-    int mode;
-    int units_per_thread;
-    int blocks;            // persistent grid size
+    const uint16_t *in = nullptr;
+    uint16_t *out = nullptr;
+    const long long *offsets = nullptr;
+    long long count = 0;
+    long long *first_bad = nullptr;  // kModeCheck only
+    int mode = kModeOut;
+    int units_per_thread = 4;
+    bool prefetch = false;
+    int blocks = 1;                  // persistent grid size
 };
 
 cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream);
-const void *batch_kernel_for_occupancy(int mode, int u);
+const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch = false);
 
 // Initialise a pool of scratch slots (min = all ones, done = 0).
 cudaError_t init_slots(Slot *slots, int count, cudaStream_t stream);

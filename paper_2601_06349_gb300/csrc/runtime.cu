@@ -1,6 +1,7 @@
 // Host runtime of libutf16wf: per-device context (SM count, occupancy-derived
-// persistent grid sizes, scratch slots, staging for host buffers), argument
-// validation and the C-ABI entry points declared in include/utf16wf.h.
+// persistent grid sizes, scratch slots, launch configuration, staging for
+// host buffers), argument validation and the C-ABI entry points declared in
+// include/utf16wf.h.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -28,17 +29,26 @@ static int env_int(const char *name, int dflt) {
     return atoi(s);
 }
 
-int DeviceCtx::blocks_for(const void *fn) {
+int bucket_of(int64_t v) {
+    int b = 0;
+    while (v > 1 && b < kBuckets - 1) {
+        v >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+int DeviceCtx::per_sm(const void *fn, size_t smem) {
+    std::lock_guard<std::mutex> lk(mu);
     auto it = occupancy.find(fn);
     if (it != occupancy.end()) return it->second;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlockThreads, 0) != cudaSuccess || per_sm < 1) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlockThreads, smem) != cudaSuccess || n < 1) {
         cudaGetLastError();
-        per_sm = 1;
+        n = 1;
     }
-    const int blocks = per_sm * sms;
-    occupancy[fn] = blocks;
-    return blocks;
+    occupancy[fn] = n;
+    return n;
 }
 
 int DeviceCtx::slot_for(cudaStream_t s, Slot **out) {
@@ -53,6 +63,27 @@ int DeviceCtx::slot_for(cudaStream_t s, Slot **out) {
     slot_of[s] = idx;
     *out = slots + idx;
     return UTF16_OK;
+}
+
+utf16_config DeviceCtx::single_config(int64_t n) {
+    std::lock_guard<std::mutex> lk(mu);
+    const int b = bucket_of(n);
+    return single_has[b] ? single_tuned[b] : def;
+}
+
+utf16_config DeviceCtx::batch_config(int64_t units, int64_t count) {
+    (void)units;
+    std::lock_guard<std::mutex> lk(mu);
+    const int b = bucket_of(count);
+    return batch_has[b] ? batch_tuned[b] : def;
+}
+
+static bool config_valid(const utf16_config &c) {
+    return c.single_variant >= 0 && c.single_variant <= 2 &&
+           (c.single_units_per_thread == 2 || c.single_units_per_thread == 4) && c.single_blocks_per_sm >= 0 &&
+           c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
+           (c.batch_prefetch == 0 || c.batch_prefetch == 1) && c.batch_blocks_per_sm >= 0 &&
+           c.batch_blocks_per_sm <= 64;
 }
 
 int get_ctx(DeviceCtx **out) {
@@ -73,6 +104,10 @@ int get_ctx(DeviceCtx **out) {
         cudaGetLastError();
         return UTF16_ECUDA;
     }
+    if (prepare_single_tma() != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
     if (cudaMalloc((void **)&c->slots, sizeof(Slot) * kSlotCount) != cudaSuccess) {
         cudaGetLastError();
         return UTF16_ENOMEM;
@@ -84,11 +119,40 @@ int get_ctx(DeviceCtx **out) {
         return UTF16_ECUDA;
     }
     cudaStreamDestroy(s);
-    c->single_u = std::max(1, std::min(4, env_int("UTF16WF_SINGLE_U", 4)));
-    c->batch_u = std::max(1, std::min(4, env_int("UTF16WF_BATCH_U", 4)));
+    utf16_config d;
+    d.single_variant = env_int("UTF16WF_SINGLE_VARIANT", kVariantTma);
+    d.single_units_per_thread = env_int("UTF16WF_SINGLE_U", 4);
+    d.single_blocks_per_sm = env_int("UTF16WF_SINGLE_BLOCKS_PER_SM", 0);
+    d.batch_units_per_thread = env_int("UTF16WF_BATCH_U", 4);
+    d.batch_prefetch = env_int("UTF16WF_BATCH_PREFETCH", 0);
+    d.batch_blocks_per_sm = env_int("UTF16WF_BATCH_BLOCKS_PER_SM", 0);
+    if (!config_valid(d)) d = utf16_config{kVariantTma, 4, 0, 4, 0, 0};
+    c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);
     return UTF16_OK;
+}
+
+void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) {
+    L.variant = cfg.single_variant;
+    // The read-only check streams 2 bytes per unit and measured faster with
+    // 128-bit loads than through the shared-memory ring on GB300.
+    if (L.mode == kModeCheck && L.variant == kVariantTma) L.variant = kVariantLdg;
+    L.units_per_thread = cfg.single_units_per_thread;
+    const bool fb = L.first_bad || L.mode == kModeCheck;
+    const bool tma = L.variant == kVariantTma;
+    const void *fn = single_kernel_for_occupancy(L.mode, fb, L.units_per_thread, L.variant);
+    const int fit = ctx->per_sm(fn, tma ? single_tma_smem_bytes() : 0);
+    const int per = cfg.single_blocks_per_sm > 0 ? std::min(cfg.single_blocks_per_sm, fit) : fit;
+    L.max_blocks = per * ctx->sms;
+}
+
+void configure_batch(DeviceCtx *ctx, const utf16_config &cfg, BatchLaunch &L) {
+    L.units_per_thread = cfg.batch_units_per_thread;
+    L.prefetch = cfg.batch_prefetch != 0;
+    const int fit = ctx->per_sm(batch_kernel_for_occupancy(L.mode, L.units_per_thread, L.prefetch), 0);
+    const int per = cfg.batch_blocks_per_sm > 0 ? std::min(cfg.batch_blocks_per_sm, fit) : fit;
+    L.blocks = per * ctx->sms;
 }
 
 static bool is_device_ptr(const void *p) {
@@ -126,8 +190,7 @@ int run_single(const uint16_t *in, uint16_t *out, int64_t n, int mode, int64_t *
     L.n = n;
     L.mode = mode;
     L.first_bad = fb;
-    L.units_per_thread = ctx->single_u;
-    L.max_blocks = ctx->blocks_for(single_kernel_for_occupancy(mode, fb, ctx->single_u));
+    configure_single(ctx, ctx->single_config(n), L);
     L.slot = slot;
     L.result = fb ? (fb_on_device ? (long long *)first_bad : &slot->result) : nullptr;
     L.lead = lead;
@@ -160,7 +223,7 @@ static int empty_first_bad(int64_t *first_bad, cudaStream_t stream) {
 }
 
 int run_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t count, int mode, int64_t *first_bad,
-              cudaStream_t stream, int units_per_thread) {
+              cudaStream_t stream) {
     DeviceCtx *ctx;
     int rc = get_ctx(&ctx);
     if (rc) return rc;
@@ -171,8 +234,7 @@ int run_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t
     L.count = count;
     L.first_bad = (long long *)first_bad;
     L.mode = mode;
-    L.units_per_thread = units_per_thread > 0 ? units_per_thread : ctx->batch_u;
-    L.blocks = ctx->blocks_for(batch_kernel_for_occupancy(mode, L.units_per_thread));
+    configure_batch(ctx, ctx->batch_config(0, count), L);
     if (launch_batch(L, stream) != cudaSuccess) {
         cudaGetLastError();
         return UTF16_ECUDA;
@@ -205,11 +267,16 @@ int utf16_init_device(void) {
     DeviceCtx *ctx;
     int rc = get_ctx(&ctx);
     if (rc) return rc;
-    for (int mode = 0; mode < 3; ++mode) {
-        ctx->blocks_for(single_kernel_for_occupancy(mode, true, ctx->single_u));
-        ctx->blocks_for(single_kernel_for_occupancy(mode, false, ctx->single_u));
-        ctx->blocks_for(batch_kernel_for_occupancy(mode, ctx->batch_u));
-    }
+    for (int mode = 0; mode < 3; ++mode)
+        for (int fb = 0; fb < 2; ++fb) {
+            SingleLaunch L;
+            L.mode = mode;
+            L.first_bad = fb != 0;
+            configure_single(ctx, ctx->def, L);
+            BatchLaunch B;
+            B.mode = mode;
+            configure_batch(ctx, ctx->def, B);
+        }
     return UTF16_OK;
 }
 
@@ -235,6 +302,35 @@ int utf16_release_device(void) {
     if (c->slots) cudaFree(c->slots);
     c->slots = nullptr;
     return UTF16_OK;
+}
+
+int utf16_get_config(utf16_config *cfg) {
+    if (!cfg) return UTF16_EINVAL;
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *cfg = ctx->def;
+    return UTF16_OK;
+}
+
+int utf16_set_config(const utf16_config *cfg) {
+    if (!cfg || !config_valid(*cfg)) return UTF16_EINVAL;
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->def = *cfg;
+    for (int b = 0; b < kBuckets; ++b) ctx->single_has[b] = ctx->batch_has[b] = false;
+    return UTF16_OK;
+}
+
+int utf16_check_device_errors(void) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    return read_and_clear_tma_timeout() ? UTF16_ETIMEOUT : UTF16_OK;
 }
 
 int utf16_to_well_formed(const uint16_t *in, uint16_t *out, int64_t n, utf16_stream_t stream) {
@@ -274,7 +370,7 @@ int utf16_to_well_formed_batch(const uint16_t *in, uint16_t *out, const int64_t 
     if (num_strings == 0) return UTF16_OK;
     if (!in || !out || !offsets || misaligned(in) || misaligned(out) || ((uintptr_t)offsets & 7u)) return UTF16_EINVAL;
     return run_batch(in, out, offsets, num_strings, in == out ? kModeInPlace : kModeOut, nullptr,
-                     (cudaStream_t)stream, 0);
+                     (cudaStream_t)stream);
 }
 
 int utf16_to_well_formed_batch_inplace(uint16_t *buf, const int64_t *offsets, int64_t num_strings,
@@ -282,7 +378,7 @@ int utf16_to_well_formed_batch_inplace(uint16_t *buf, const int64_t *offsets, in
     if (num_strings < 0) return UTF16_EINVAL;
     if (num_strings == 0) return UTF16_OK;
     if (!buf || !offsets || misaligned(buf) || ((uintptr_t)offsets & 7u)) return UTF16_EINVAL;
-    return run_batch(buf, buf, offsets, num_strings, kModeInPlace, nullptr, (cudaStream_t)stream, 0);
+    return run_batch(buf, buf, offsets, num_strings, kModeInPlace, nullptr, (cudaStream_t)stream);
 }
 
 int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64_t num_strings, int64_t *first_bad,
@@ -291,7 +387,7 @@ int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64
     if (num_strings == 0) return UTF16_OK;
     if (!in || !offsets || !first_bad || misaligned(in) || ((uintptr_t)offsets & 7u) || ((uintptr_t)first_bad & 7u))
         return UTF16_EINVAL;
-    return run_batch(in, nullptr, offsets, num_strings, kModeCheck, first_bad, (cudaStream_t)stream, 0);
+    return run_batch(in, nullptr, offsets, num_strings, kModeCheck, first_bad, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <unordered_map>
 
+#include "../../include/utf16wf.h"
 #include "device.cuh"
 #include "internal.h"
 
@@ -14,17 +15,25 @@ namespace u16wf {
 
 constexpr int kSlotCount = 4096;
 constexpr int kHostLanes = 3;
+constexpr int kBuckets = 64;  // log2 size buckets for tuned launch configurations
 
 struct DeviceCtx {
     int device = 0;
     int sms = 1;
-    int single_u = 4;
-    int batch_u = 4;
     std::mutex mu;
     Slot *slots = nullptr;  // device pool of kSlotCount slots
     int slots_used = 0;
     std::unordered_map<cudaStream_t, int> slot_of;
-    std::unordered_map<const void *, int> occupancy;  // kernel -> persistent grid size
+    std::unordered_map<const void *, int> occupancy;  // kernel -> resident blocks per SM
+
+    // Launch configuration: the default, and per log2 bucket what the
+    // autotuner measured best (single strings: bucket of n; batches: bucket
+    // of the mean string length).
+    utf16_config def;
+    utf16_config single_tuned[kBuckets];
+    bool single_has[kBuckets] = {};
+    utf16_config batch_tuned[kBuckets];
+    bool batch_has[kBuckets] = {};
 
     // Host-buffer pipeline: kHostLanes streams, each with a device staging
     // buffer of `stage_units` units; pinned per-chunk first-error results.
@@ -35,13 +44,20 @@ struct DeviceCtx {
     int64_t *chunk_first = nullptr;  // pinned host
     int64_t chunk_first_cap = 0;
 
-    int blocks_for(const void *fn);
+    int per_sm(const void *fn, size_t smem);
     int slot_for(cudaStream_t s, Slot **out);
     int ensure_staging(int64_t units, int64_t chunks);
     void release_staging();
+    utf16_config single_config(int64_t n);
+    utf16_config batch_config(int64_t units, int64_t count);
 };
 
 int get_ctx(DeviceCtx **out);
+int bucket_of(int64_t v);
+
+// Fill a single-string launch from a configuration (grid size included).
+void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L);
+void configure_batch(DeviceCtx *ctx, const utf16_config &cfg, BatchLaunch &L);
 
 // Single-string launch with optional first-error output (host or device
 // pointer) and outside neighbours `lead` / `trail` (0 = none).
@@ -49,6 +65,6 @@ int run_single(const uint16_t *in, uint16_t *out, int64_t n, int mode, int64_t *
                uint32_t lead, uint32_t trail);
 
 int run_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t count, int mode, int64_t *first_bad,
-              cudaStream_t stream, int units_per_thread);
+              cudaStream_t stream);
 
 }  // namespace u16wf

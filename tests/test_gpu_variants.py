@@ -1,0 +1,105 @@
+"""Every launch configuration gives the oracle's result, bit-exact: the
+single-string kernel with 128-bit loads (with and without next-chunk
+prefetch, 2 or 4 vectors per thread), the TMA-staged kernel, reduced grids,
+and the batch kernel with 2 or 4 vectors per thread, with and without
+prefetch.  Also the autotuner's choice, and that no kernel gave up a bounded
+wait."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import Guarded, first_diff, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+SINGLE = [(0, 4, 0), (0, 2, 0), (1, 4, 0), (1, 2, 0), (2, 4, 0), (2, 4, 1), (0, 4, 1), (1, 2, 2)]
+BATCH = [(4, 0, 0), (2, 0, 0), (4, 1, 0), (2, 1, 0), (4, 0, 1)]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2601_06349_gb300 as p
+    p.init_device()
+    saved = p.get_config()
+    yield p
+    p.set_config(saved)
+
+
+@pytest.fixture(scope="module")
+def strings():
+    big = workloads.mixed(40_000_123, 1e-2, seed=31)
+    shifted = workloads.shifted_alternating(20_000_003)
+    clean = workloads.mixed(30_000_001, 0.0, seed=32)
+    return {"mixed": (big, oracle.to_well_formed_threads(big), oracle.first_bad(big)),
+            "shifted": (shifted, oracle.to_well_formed_threads(shifted), oracle.first_bad(shifted)),
+            "clean": (clean, clean, clean.size)}
+
+
+@pytest.mark.parametrize("variant,u,bps", SINGLE)
+def test_single_configurations(pkg, strings, variant, u, bps):
+    import torch
+    pkg.set_config(single_variant=variant, single_units_per_thread=u, single_blocks_per_sm=bps)
+    for name, (src, want, want_fb) in strings.items():
+        for a_in, a_out in ((0, 0), (3, 3), (5, 1)):
+            gi = Guarded(src.size, a_in, src)
+            go = Guarded(src.size, a_out)
+            _, fb = pkg.to_well_formed_first_bad(gi.view, go.view)
+            got = go.get()
+            assert np.array_equal(got, want), (name, variant, u, a_in, a_out, first_diff(got, want))
+            assert int(fb.item()) == want_fb, (name, variant, u)
+            assert go.canaries_ok()
+            assert pkg.first_error_index_sync(gi.view) == want_fb, (name, variant, u)
+            pkg.to_well_formed_(gi.view)
+            assert np.array_equal(gi.get(), want), (name, variant, u, "in place")
+            assert gi.canaries_ok()
+    # small strings around the tile edges of the TMA kernel (8192 units)
+    rng = np.random.default_rng(variant * 10 + u)
+    alph = np.array([0x41, 0xD800, 0xDBFF, 0xDC00, 0xDFFF, 0xFFFD], np.uint16)
+    for n in (1, 7, 8, 9, 8191, 8192, 8193, 16383, 16384, 16385, 16400, 24583, 40961):
+        uu = alph[rng.integers(0, alph.size, n)]
+        want = oracle.to_well_formed(uu)
+        for a in (0, 1, 7):
+            gi = Guarded(n, a, uu)
+            go = Guarded(n, a)
+            _, fb = pkg.to_well_formed_first_bad(gi.view, go.view)
+            assert np.array_equal(go.get(), want), (n, a, variant, u)
+            assert int(fb.item()) == oracle.first_bad(uu)
+            assert pkg.first_error_index_sync(gi.view) == oracle.first_bad(uu)
+    torch.cuda.synchronize()
+    pkg.check_device_errors()
+
+
+@pytest.mark.parametrize("u,pf,bps", BATCH)
+def test_batch_configurations(pkg, u, pf, bps):
+    pkg.set_config(batch_units_per_thread=u, batch_prefetch=pf, batch_blocks_per_sm=bps)
+    from test_gpu_batch import _run_all_forms
+    units, offs = workloads.ragged_batch(count=200_000, seed=77)
+    _run_all_forms(pkg, units, offs, 0, 0, f"batch u={u} pf={pf}")
+    _run_all_forms(pkg, units, offs, 3, 6, f"batch u={u} pf={pf} misaligned")
+    pkg.check_device_errors()
+
+
+def test_autotuner_choice_is_correct(pkg):
+    import torch
+    u = workloads.mixed(64 << 20, 1e-2, seed=51)
+    d = to_dev(u)
+    out = torch.empty_like(d)
+    cfg = pkg.autotune_single(d, out, reps=3)
+    assert cfg.single_variant in (0, 1, 2)
+    out.zero_()
+    _, fb = pkg.to_well_formed_first_bad(d, out)
+    assert np.array_equal(to_host(out), oracle.to_well_formed_threads(u))
+    assert int(fb.item()) == oracle.first_bad(u)
+    units, offs = workloads.ragged_batch(count=300_000, seed=52)
+    du = to_dev(units)
+    do = torch.from_numpy(offs).cuda()
+    bcfg = pkg.autotune_batch(du, do, reps=3)
+    assert bcfg.batch_units_per_thread in (2, 4)
+    got = to_host(pkg.to_well_formed_batch(du, do))
+    assert np.array_equal(got, oracle.to_well_formed_batch(units, offs))
+    pkg.check_device_errors()
