@@ -54,7 +54,59 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip the variant / ragged / e2e measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4000,
+                    help="requests per arrival rate in the serving sweep")
+    ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), default=None,
+                    help="run a small case of one kernel (256 MiB string or the ragged batch) six times and exit; "
+                         "for ncu captures, prints no benchmark line")
     return ap.parse_args()
+
+
+NCU_CASES = {"single_out_fb", "single_out", "single_check", "single_inplace", "batch_out", "batch_check",
+             "batch_inplace"}
+
+
+def run_ncu_case(name):
+    """Six launches of one kernel on a case small enough for a full ncu
+    capture (256 MiB mixed string at 1e-2 lone rate, or the 1,000,000-string
+    ragged batch).  The launch configuration is the library default (override
+    with the UTF16WF_* environment variables)."""
+    import torch
+    import paper_2601_06349_gb300 as wf
+    wf.init_device()
+    if name.startswith("single"):
+        u = workloads.mixed(1 << 27, 1e-2 if name != "single_check" else 0.0, seed=99)
+        d = torch.from_numpy(u.view(np.int16)).cuda()
+        o = torch.empty_like(d)
+        fb = torch.empty(1, dtype=torch.int64, device="cuda")
+        for _ in range(6):
+            if name == "single_out_fb":
+                wf.to_well_formed_first_bad(d, o, fb)
+            elif name == "single_out":
+                wf.to_well_formed(d, o)
+            elif name == "single_check":
+                wf.first_error_index(d, fb)
+            else:
+                o.copy_(d)
+                wf.to_well_formed_(o)
+    else:
+        units, offs = workloads.ragged_batch()
+        d = torch.from_numpy(units.view(np.int16)).cuda()
+        do = torch.from_numpy(offs).cuda()
+        o = torch.empty_like(d)
+        fbb = torch.empty(offs.size - 1, dtype=torch.int64, device="cuda")
+        for _ in range(6):
+            if name == "batch_out":
+                wf.to_well_formed_batch(d, do, o)
+            elif name == "batch_check":
+                wf.first_error_index_batch(d, do, fbb)
+            else:
+                o.copy_(d)
+                wf.to_well_formed_batch_(o, do)
+    torch.cuda.synchronize()
+    wf.check_device_errors()
+    print(f"ncu case {name} ok")
+    return 0
 
 
 # ------------------------------------------------------------------ helpers
@@ -234,6 +286,8 @@ def run_reference(args):
 # --------------------------------------------------------------- GPU arm
 def main():
     args = parse()
+    if args.ncu_case:
+        return run_ncu_case(args.ncu_case)
     if args.impl == "reference":
         return run_reference(args)
     rank, world, local = dist_env()
@@ -311,6 +365,7 @@ def main():
         del d_in, d_out
         torch.cuda.empty_cache()
         line["ragged"] = ragged_measure(torch, wf, stream)
+        line["serve"] = serve_measure(torch, wf, args.serve_requests)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(u)
     if dist:
@@ -451,6 +506,56 @@ def ragged_measure(torch, wf, stream):
                                       "input_gbs": round(sample_units * 2 / (ms_ps * 1e-3) / 1e9, 3),
                                       "strings_per_s": round(sample / (ms_ps * 1e-3), 1)}
     res["batch_strings_per_s"] = round((offs.size - 1) / (ms * 1e-3), 1)
+    return res
+
+
+def serve_measure(torch, wf, count):
+    """Serving loop: requests of 80% U[16,256], 19% U[1K,64K], 1% U[1M,16M]
+    units, mixed content at 1e-3 lone rate, pinned host buffers, 4 GiB HBM
+    budget.  Capacity = all requests submitted at once; then Poisson arrivals
+    at fractions of that capacity through the continuous-batching engine and
+    through one plain launch per request."""
+    lens = workloads.request_lengths(count)
+    reqs = [workloads.mixed(int(n), 1e-3, seed=workloads.SEED_BASE + 4 + i) for i, n in enumerate(lens)]
+    ins = [torch.from_numpy(u.view(np.int16)).pin_memory() for u in reqs]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    units = int(lens.sum())
+
+    def summarize(lat, wall):
+        return {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                "strings_per_s": round(count / wall, 1), "input_gbs": round(units * 2 / wall / 1e9, 2)}
+
+    res = {"requests": count, "units": units, "mean_request_bytes": round(units * 2 / count, 1),
+           "hbm_budget_bytes": 4 << 30, "host_buffers": "pinned"}
+    with wf.Server(hbm_budget_bytes=4 << 30) as srv:
+        srv.replay(ins[:200], outs[:200], 0, seed=9)  # warm-up
+        t0 = time.perf_counter()
+        lat, fb = srv.replay(ins, outs, 0, seed=10)
+        wall = time.perf_counter() - t0
+        cap = count / wall
+        res["capacity"] = summarize(lat, wall)
+        res["capacity"]["batches"] = srv.stats()["batches"]
+        sweep = []
+        for frac in (0.25, 0.5, 0.75, 0.9):
+            rate = frac * cap
+            t0 = time.perf_counter()
+            lat, fb = srv.replay(ins, outs, rate, seed=11)
+            wall = time.perf_counter() - t0
+            sweep.append({"rate_frac": frac, "rate_per_s": round(rate, 1), **summarize(lat, wall)})
+        res["batched"] = sweep
+    t0 = time.perf_counter()
+    lat, fb = wf.plain_replay(ins, outs, 0, seed=10)
+    wall = time.perf_counter() - t0
+    res["plain_capacity"] = summarize(lat, wall)
+    plain = []
+    for frac in (0.25, 0.5):
+        rate = frac * cap
+        t0 = time.perf_counter()
+        lat, fb = wf.plain_replay(ins, outs, rate, seed=11)
+        wall = time.perf_counter() - t0
+        plain.append({"rate_frac": frac, "rate_per_s": round(rate, 1), **summarize(lat, wall)})
+    res["plain"] = plain
     return res
 
 

@@ -68,6 +68,7 @@ typedef struct CUstream_st *utf16_stream_t;
 #define UTF16_ECLOSED (-6)  /* the serving engine is shut down */
 #define UTF16_EAGAIN (-7)   /* nothing ready yet (non-blocking poll) */
 #define UTF16_ETOOBIG (-8)  /* input longer than the no-allocation entry point's stated maximum */
+#define UTF16_ECANCELED (-9) /* serving request cancelled before admission */
 
 /* Human-readable text of a status code (static storage, never NULL). */
 const char *utf16_strerror(int code);
@@ -212,6 +213,102 @@ int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int64_t *offse
  * device.
  */
 int utf16_check_device_errors(void);
+
+/* ===================================================================== *
+ * Serving: continuous batching of repair requests (host strings).
+ *
+ * Not in the paper; the paper's function repairs one string at a time.
+ * Requests arrive through utf16_server_submit at any time.  A scheduler
+ * thread admits them in arrival order against a device arena of
+ * `hbm_budget_bytes` (a FIFO ring) and launches whatever has arrived as one
+ * ragged batch as soon as one of `max_inflight_batches` batch slots is free
+ * -- it never waits for a batch to fill.  Each batch is copied in, repaired
+ * in place with the per-string first-error index, and copied out on three
+ * streams ordered by events, so transfers of one batch overlap the kernel of
+ * the next.  Small requests (< small_request_bytes) are packed through a
+ * pinned staging buffer per slot; larger ones are copied straight from and to
+ * the caller's buffers (pinned buffers overlap; pageable ones are copied
+ * synchronously by the CUDA runtime).  Each string of a batch is repaired on
+ * its own, so a request's result is the same alone and in any mix.
+ * ===================================================================== */
+typedef struct utf16_server utf16_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;     /* device arena for admitted batches (>= 1 MiB) */
+    int64_t max_batch_strings;    /* strings per launched batch (requests count at most 2 each) */
+    int64_t max_batch_bytes;      /* input bytes per launched batch; also the largest request */
+    int max_inflight_batches;     /* batches between admission and completion (1..64) */
+    int64_t staging_bytes;        /* pinned host staging per batch slot */
+    int64_t small_request_bytes;  /* requests below this size are packed through staging */
+    int64_t inject_fail_mod;      /* testing: 0 = off; k > 0 = the admission of every request whose
+                                     ticket % k == k - 1 fails with UTF16_ENOMEM (host-side fault
+                                     injection; other requests are unaffected) */
+} utf16_server_options;
+
+typedef struct {
+    uint64_t ticket;
+    int64_t first_bad;   /* first-error index of the request's string (n if well formed) */
+    int64_t n;
+    int64_t arrival_ns;  /* utf16_server_clock_ns() time the request counts from */
+    int64_t done_ns;     /* time its result was in the caller's buffer */
+    int status;          /* UTF16_OK, UTF16_ENOMEM (rejected), UTF16_ECANCELED, UTF16_ECLOSED, UTF16_ECUDA */
+} utf16_completion;
+
+typedef struct {
+    int64_t batches, completed, rejected, units;
+    int64_t max_batch_requests;
+    int64_t pending, inflight_batches, arena_used_bytes;
+} utf16_server_stats;
+
+/* Defaults: 4 GiB budget, 65536 strings / 256 MiB per batch, 4 slots, 64 MiB staging, 256 KiB small limit. */
+int utf16_server_default_options(utf16_server_options *opt);
+/* Allocates the arena, staging and streams on the current device; starts two host threads. */
+int utf16_server_create(const utf16_server_options *opt, utf16_server **server);
+/* Monotonic clock (ns) the server's timestamps use. */
+int64_t utf16_server_clock_ns(void);
+/*
+ * Queue one string.  host_in / host_out: [n] host buffers (may be the same),
+ * valid until the request completes.  arrival_ns: the time latency counts
+ * from (utf16_server_clock_ns(); 0 = now).  Non-blocking.  A request that
+ * cannot fit an empty arena, batch or staging buffer returns UTF16_ENOMEM.
+ */
+int utf16_server_submit(utf16_server *server, const uint16_t *host_in, uint16_t *host_out, int64_t n,
+                        int64_t arrival_ns, uint64_t *ticket);
+/* Remove a request that has not been admitted yet (completes with UTF16_ECANCELED); UTF16_EAGAIN if it has. */
+int utf16_server_cancel(utf16_server *server, uint64_t ticket);
+/* Next completion (any order of tickets).  timeout_us: 0 = poll (UTF16_EAGAIN), < 0 = up to an hour,
+ * else the bound (UTF16_ETIMEOUT). */
+int utf16_server_next(utf16_server *server, utf16_completion *completion, int64_t timeout_us);
+int utf16_server_stats_get(utf16_server *server, utf16_server_stats *stats);
+/* Stops admission, completes pending requests with UTF16_ECLOSED, waits for in-flight batches, frees all. */
+int utf16_server_destroy(utf16_server *server);
+
+/*
+ * Load replay (benchmarking): submit `count` requests with exponential
+ * inter-arrival times at `rate_per_s` (xoshiro256** seeded with `seed`;
+ * rate <= 0: all at once), each latency counted from its scheduled arrival,
+ * and wait for all.  Outputs per request index: latency_s (done - arrival)
+ * and first_bad (status < 0 stored as the status).  Blocking.
+ *   utf16_server_replay  through a serving engine (continuous batching);
+ *   utf16_plain_replay   one plain launch per request in arrival order:
+ *                        H2D, fused repair + first-error kernel, D2H, wait.
+ */
+int utf16_server_replay(utf16_server *server, const uint16_t *const *inputs, uint16_t *const *outputs,
+                        const int64_t *lengths, int64_t count, double rate_per_s, uint64_t seed, double *latency_s,
+                        int64_t *first_bad);
+int utf16_plain_replay(const uint16_t *const *inputs, uint16_t *const *outputs, const int64_t *lengths, int64_t count,
+                       double rate_per_s, uint64_t seed, double *latency_s, int64_t *first_bad);
+
+/*
+ * FIFO ring allocator used for serving admission, exposed for reuse and for
+ * testing: offsets in [0, capacity); blocks are freed oldest first.
+ */
+typedef struct utf16_arena utf16_arena;
+int utf16_arena_create(int64_t capacity, utf16_arena **arena);
+int64_t utf16_arena_alloc(utf16_arena *arena, int64_t size); /* offset, or -1 if it does not fit */
+int utf16_arena_free_oldest(utf16_arena *arena);
+int64_t utf16_arena_used(const utf16_arena *arena);
+int utf16_arena_destroy(utf16_arena *arena);
 
 /*
  * Prepare the current device (SM count, occupancy, scratch pool, launch

@@ -42,6 +42,25 @@ class Config(ctypes.Structure):
 
 
 VARIANT_LDG, VARIANT_LDG_PREFETCH, VARIANT_TMA = 0, 1, 2
+ECANCELED = -9
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_batch_strings", ctypes.c_int64),
+                ("max_batch_bytes", ctypes.c_int64), ("max_inflight_batches", ctypes.c_int),
+                ("staging_bytes", ctypes.c_int64), ("small_request_bytes", ctypes.c_int64),
+                ("inject_fail_mod", ctypes.c_int64)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("first_bad", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("arrival_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64), ("status", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("units", ctypes.c_int64), ("max_batch_requests", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("inflight_batches", ctypes.c_int64), ("arena_used_bytes", ctypes.c_int64)]
 
 
 def _declare(lib):
@@ -66,6 +85,21 @@ def _declare(lib):
         "utf16_check_device_errors": ([], ctypes.c_int),
         "utf16_to_well_formed_first_bad_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "utf16_release_device": ([], ctypes.c_int),
+        "utf16_server_default_options": ([ctypes.POINTER(ServerOptions)], ctypes.c_int),
+        "utf16_server_create": ([ctypes.POINTER(ServerOptions), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "utf16_server_clock_ns": ([], ctypes.c_int64),
+        "utf16_server_submit": ([vp, vp, vp, i64, i64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "utf16_server_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
+        "utf16_server_next": ([vp, ctypes.POINTER(Completion), i64], ctypes.c_int),
+        "utf16_server_stats_get": ([vp, ctypes.POINTER(ServerStats)], ctypes.c_int),
+        "utf16_server_destroy": ([vp], ctypes.c_int),
+        "utf16_server_replay": ([vp, vp, vp, vp, i64, ctypes.c_double, ctypes.c_uint64, vp, vp], ctypes.c_int),
+        "utf16_plain_replay": ([vp, vp, vp, i64, ctypes.c_double, ctypes.c_uint64, vp, vp], ctypes.c_int),
+        "utf16_arena_create": ([i64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "utf16_arena_alloc": ([vp, i64], ctypes.c_int64),
+        "utf16_arena_free_oldest": ([vp], ctypes.c_int),
+        "utf16_arena_used": ([vp], ctypes.c_int64),
+        "utf16_arena_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -318,3 +352,145 @@ def autotune_batch(units, offsets, out=None, reps: int = 5) -> Config:
 def check_device_errors():
     """Raise if a kernel gave up a bounded wait since the last check."""
     _check(lib().utf16_check_device_errors(), "utf16_check_device_errors")
+
+
+# ------------------------------------------------------------------ serving
+def _host_ptr(buf):
+    """(address, units) of a host buffer: numpy uint16 array or CPU tensor."""
+    import numpy as np
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.uint16 or not buf.flags.c_contiguous:
+            raise TypeError("host buffers must be contiguous uint16 arrays")
+        return buf.ctypes.data, buf.size
+    torch = _torch()
+    if buf.is_cuda or buf.dtype not in (torch.uint16, torch.int16):
+        raise TypeError("host buffers must be CPU tensors of 16-bit units")
+    return buf.data_ptr(), buf.numel()
+
+
+class Server:
+    """Continuous-batching repair engine on the current device (see
+    utf16_server_* in include/utf16wf.h).  Host buffers given to submit() are
+    kept referenced here until their completion has been returned by next()."""
+
+    def __init__(self, **options):
+        o = ServerOptions()
+        _check(lib().utf16_server_default_options(ctypes.byref(o)), "utf16_server_default_options")
+        for k, v in options.items():
+            setattr(o, k, int(v))
+        h = ctypes.c_void_p()
+        _check(lib().utf16_server_create(ctypes.byref(o), ctypes.byref(h)), "utf16_server_create")
+        self._h = h
+        self._refs = {}
+        self.options = o
+
+    def submit(self, host_in, host_out, arrival_ns: int = 0) -> int:
+        pin, n = _host_ptr(host_in)
+        pout, n2 = _host_ptr(host_out)
+        if n2 != n:
+            raise ValueError("host_out must have as many units as host_in")
+        t = ctypes.c_uint64()
+        _check(lib().utf16_server_submit(self._h, pin, pout, n, arrival_ns, ctypes.byref(t)), "utf16_server_submit")
+        self._refs[t.value] = (host_in, host_out)
+        return t.value
+
+    def cancel(self, ticket: int) -> bool:
+        rc = lib().utf16_server_cancel(self._h, ticket)
+        if rc not in (OK, EAGAIN):
+            _check(rc, "utf16_server_cancel")
+        return rc == OK
+
+    def next(self, timeout_us: int = -1):
+        c = Completion()
+        rc = lib().utf16_server_next(self._h, ctypes.byref(c), timeout_us)
+        if rc in (EAGAIN, ETIMEOUT):
+            return None
+        _check(rc, "utf16_server_next")
+        self._refs.pop(c.ticket, None)
+        return {"ticket": c.ticket, "first_bad": c.first_bad, "n": c.n, "status": c.status,
+                "latency_s": (c.done_ns - c.arrival_ns) * 1e-9}
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().utf16_server_stats_get(self._h, ctypes.byref(st)), "utf16_server_stats_get")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def replay(self, inputs, outputs, rate_per_s: float, seed: int = 1):
+        """Poisson replay of the requests through this server; returns
+        (latencies in s, first_bad or negative status) as numpy arrays."""
+        return _replay(self._h, inputs, outputs, rate_per_s, seed)
+
+    def close(self):
+        if self._h:
+            _check(lib().utf16_server_destroy(self._h), "utf16_server_destroy")
+            self._h = None
+            self._refs.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def clock_ns() -> int:
+    return lib().utf16_server_clock_ns()
+
+
+def _replay(handle, inputs, outputs, rate_per_s, seed):
+    import numpy as np
+    count = len(inputs)
+    ins = (ctypes.c_void_p * count)()
+    outs = (ctypes.c_void_p * count)()
+    lens = np.empty(count, dtype=np.int64)
+    for i, (a, b) in enumerate(zip(inputs, outputs)):
+        pa, na = _host_ptr(a)
+        pb, nb = _host_ptr(b)
+        if na != nb:
+            raise ValueError("input and output lengths differ")
+        ins[i], outs[i], lens[i] = pa, pb, na
+    lat = np.zeros(count, dtype=np.float64)
+    fb = np.zeros(count, dtype=np.int64)
+    if handle is None:
+        rc = lib().utf16_plain_replay(ins, outs, lens.ctypes.data, count, float(rate_per_s), seed,
+                                      lat.ctypes.data, fb.ctypes.data)
+    else:
+        rc = lib().utf16_server_replay(handle, ins, outs, lens.ctypes.data, count, float(rate_per_s), seed,
+                                       lat.ctypes.data, fb.ctypes.data)
+    _check(rc, "replay")
+    return lat, fb
+
+
+def plain_replay(inputs, outputs, rate_per_s: float, seed: int = 1):
+    """The same replay with one plain launch per request (H2D, fused kernel,
+    D2H, wait), in arrival order."""
+    return _replay(None, inputs, outputs, rate_per_s, seed)
+
+
+class Arena:
+    """The serving engine's FIFO ring allocator (host-side offsets only)."""
+
+    def __init__(self, capacity: int):
+        h = ctypes.c_void_p()
+        _check(lib().utf16_arena_create(capacity, ctypes.byref(h)), "utf16_arena_create")
+        self._h = h
+
+    def alloc(self, size: int) -> int:
+        return lib().utf16_arena_alloc(self._h, size)
+
+    def free_oldest(self) -> bool:
+        return lib().utf16_arena_free_oldest(self._h) == OK
+
+    def used(self) -> int:
+        return lib().utf16_arena_used(self._h)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().utf16_arena_destroy(self._h)
+            self._h = None

@@ -62,32 +62,43 @@ __device__ __forceinline__ long long lower_bound_warp(const long long *offsets, 
     return lo;
 }
 
+// This lane's U vectors of a chunk, and (lanes 0 and 31) the units just
+// before and after the chunk (0 outside [lo, hi)).
+template <int U>
+struct BatchChunk {
+    uint4 v[U];
+    uint32_t halo;
+};
+
 template <int MODE, int U>
 __device__ __forceinline__ void load_batch_chunk(const BatchArgs &A, const uint4 *vin, long long vfirst, long long lo,
-                                                 long long hi, int lane, uint4 (&v)[U]) {
+                                                 long long hi, int lane, BatchChunk<U> &ch) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     const long long cfirst = vfirst * 8 - A.a;
     if (cfirst >= lo && cfirst + CU <= hi) {
         const uint4 *p = vin + vfirst + lane;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if constexpr (MODE == kModeInPlace)
-                v[u] = ld_plain(p + 32 * u);
+            if constexpr (MODE == kModeInPlace || MODE == kModeInPlaceFirst)
+                ch.v[u] = ld_plain(p + 32 * u);
             else
-                v[u] = ld_stream(p + 32 * u);
+                ch.v[u] = ld_stream(p + 32 * u);
         }
     } else {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
-            v[u] = make_uint4(0, 0, 0, 0);
+            ch.v[u] = make_uint4(0, 0, 0, 0);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const long long p = p0 + k;
-                if (p >= lo && p < hi) vec_set_unit(v[u], k, A.in[p]);
+                if (p >= lo && p < hi) vec_set_unit(ch.v[u], k, A.in[p]);
             }
         }
     }
+    ch.halo = 0;
+    const long long hp = (lane == 0) ? cfirst - 1 : cfirst + CU;
+    if ((lane == 0 || lane == 31) && hp >= lo && hp < hi) ch.halo = A.in[hp];
 }
 
 __device__ __forceinline__ uint32_t batch_valid_bits8(long long p0, long long lo, long long hi) {
@@ -97,28 +108,40 @@ __device__ __forceinline__ uint32_t batch_valid_bits8(long long p0, long long lo
     return ((1u << b) - 1u) & ~((1u << a) - 1u);
 }
 
+template <int MODE, int ST>
+__device__ __forceinline__ void batch_store_vec(uint16_t *d, const uint4 &f, bool edge, long long p0, long long lo,
+                                                long long hi, uint32_t bad8) {
+    if (!edge) {
+        if constexpr (MODE == kModeInPlace || MODE == kModeInPlaceFirst)
+            *reinterpret_cast<uint4 *>(d) = f;
+        else
+            store_vec<ST>(d, f);
+    } else {
+        const uint32_t w8 = (MODE == kModeInPlace || MODE == kModeInPlaceFirst) ? bad8 : batch_valid_bits8(p0, lo, hi);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (w8 & (1u << k)) d[k] = (uint16_t)vec_unit(f, k);
+    }
+}
+
 template <int MODE, int ST, int U>
 __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long long cfirst, long long lo, long long hi,
-                                                    const uint4 (&v)[U], int lane, uint32_t *bits, long long &hint) {
+                                                    const BatchChunk<U> &ch, int lane, uint32_t *bits,
+                                                    long long &hint) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     constexpr int kWords = (int)(CU / 32) + 1;
     const bool edge = (cfirst < lo) || (cfirst + CU > hi);
-    const uint32_t surr = any_surrogate<U>(v);
+    const long long lfirst = cfirst + lane * kUnitsPerVec;
+    uint16_t *dst = (MODE == kModeCheck) ? nullptr : A.out + lfirst;
+    ChunkBits<U> cb;
+    const uint32_t surr = chunk_surrogates<U>(ch.v, cb);
 
     if (!__any_sync(kFull, surr != 0)) {
         if constexpr (MODE == kModeOut) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
-                if (!edge) {
-                    store_vec<ST>(A.out + p0, v[u]);
-                } else {
-                    const uint32_t w8 = batch_valid_bits8(p0, lo, hi);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (w8 & (1u << k)) A.out[p0 + k] = (uint16_t)vec_unit(v[u], k);
-                }
-            }
+            for (int u = 0; u < U; ++u)
+                batch_store_vec<MODE, ST>(dst + u * kWarpSliceUnits, ch.v[u], edge, lfirst + u * kWarpSliceUnits, lo,
+                                          hi, 0u);
         }
         return;
     }
@@ -142,17 +165,9 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
         if (m != kFull) break;
     }
     __syncwarp();
-    uint32_t hp = 0, hn = 0;
-    if (lane == 0) {
-        const long long p = cfirst - 1;
-        hp = (p >= lo && p < hi) ? unit_is_high(A.in[p]) : 0u;
-    }
-    if (lane == 31) {
-        const long long p = cfirst + CU;
-        hn = (p >= lo && p < hi) ? unit_is_low(A.in[p]) : 0u;
-    }
+
     uint32_t from_prev, from_next;
-    neighbour_bits<U>(v, hp, hn, lane, from_prev, from_next);
+    chunk_classes<U>(cb, unit_is_high(ch.halo), unit_is_low(ch.halo), lane, from_prev, from_next);
     long long prev_s = -1;
     const long long s_lo = hint > 0 ? hint - 1 : 0;
 #pragma unroll
@@ -165,32 +180,24 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
         uint32_t st_lo, st_hi;
         bits_to_flags(s9 & 0xFFu, st_lo, st_hi);
         uint32_t bad_lo, bad_hi;
-        vec_mismatch(v[u], (from_prev >> u) & 1u, (from_next >> u) & 1u, st_lo, st_hi, (s9 >> 8) & 1u, bad_lo,
-                     bad_hi);
+        vec_bad<U>(cb, u, from_prev, from_next, st_lo, st_hi, (s9 >> 8) & 1u, bad_lo, bad_hi);
         if (edge) {
             uint32_t vlo, vhi;
             bits_to_flags(batch_valid_bits8(p0, lo, hi), vlo, vhi);
             bad_lo &= vlo;
             bad_hi &= vhi;
         }
-        const bool vb = (bad_lo | bad_hi) != 0;
-        if constexpr (MODE != kModeCheck) {
-            if (MODE == kModeOut || vb) {
-                const uint4 f = vb ? fix_vec(v[u], bad_lo, bad_hi) : v[u];
-                if (!edge) {
-                    if constexpr (MODE == kModeInPlace)
-                        *reinterpret_cast<uint4 *>(A.out + p0) = f;
-                    else
-                        store_vec<ST>(A.out + p0, f);
-                } else {
-                    const uint32_t w8 = (MODE == kModeInPlace) ? (gather4(bad_lo) | (gather4(bad_hi) << 4))
-                                                               : batch_valid_bits8(p0, lo, hi);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (w8 & (1u << k)) A.out[p0 + k] = (uint16_t)vec_unit(f, k);
-                }
-            }
-        } else {
+        const uint32_t vbad = bad_lo | bad_hi;
+        if constexpr (MODE == kModeOut) {
+            uint4 f = ch.v[u];
+            if (vbad) f = fix_vec(f, bad_lo, bad_hi);
+            batch_store_vec<MODE, ST>(dst + u * kWarpSliceUnits, f, edge, p0, lo, hi, 0u);
+        } else if constexpr (MODE == kModeInPlace || MODE == kModeInPlaceFirst) {
+            if (vbad)
+                batch_store_vec<MODE, ST>(dst + u * kWarpSliceUnits, fix_vec(ch.v[u], bad_lo, bad_hi), edge, p0, lo,
+                                          hi, gather4(bad_lo) | (gather4(bad_hi) << 4));
+        }
+        if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
             // Per-string first-error index: the first bad unit of each string
             // within this thread's units, one atomic per (thread, string).
             uint32_t rest = gather4(bad_lo) | (gather4(bad_hi) << 4);
@@ -238,12 +245,10 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
 
     long long hint = 0;
     if constexpr (PF) {
-        uint4 nv[U];
+        BatchChunk<U> nv;
         if (c_begin < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + c_begin * (32LL * U), lo, hi, lane, nv);
         for (long long c = c_begin; c < c_end; ++c) {
-            uint4 v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = nv[u];
+            const BatchChunk<U> v = nv;
             if (c + 1 < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + (c + 1) * (32LL * U), lo, hi, lane, nv);
             const long long cfirst = (vbeg + c * (32LL * U)) * 8 - A.a;
             process_batch_chunk<MODE, ST, U>(A, cfirst, lo, hi, v, lane, bits, hint);
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
     } else {
         for (long long c = c_begin; c < c_end; ++c) {
             const long long vfirst = vbeg + c * (32LL * U);
-            uint4 v[U];
+            BatchChunk<U> v;
             load_batch_chunk<MODE, U>(A, vin, vfirst, lo, hi, lane, v);
             process_batch_chunk<MODE, ST, U>(A, vfirst * 8 - A.a, lo, hi, v, lane, bits, hint);
         }
@@ -273,6 +278,7 @@ static const void *batch_ptr(int u, bool pf) {
 
 static const void *pick_batch(int mode, int st, int u, bool pf) {
     if (mode == kModeCheck) return batch_ptr<kModeCheck, 16>(u, pf);
+    if (mode == kModeInPlaceFirst) return batch_ptr<kModeInPlaceFirst, 16>(u, pf);
     if (mode == kModeInPlace) return batch_ptr<kModeInPlace, 16>(u, pf);
     switch (st) {
         case 16: return batch_ptr<kModeOut, 16>(u, pf);
@@ -295,7 +301,7 @@ cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream) {
         const unsigned rel = (unsigned)(((uintptr_t)L.out - (uintptr_t)L.in) & 15u);
         st = (rel == 0) ? 16 : (rel == 8) ? 8 : (rel % 4 == 0) ? 4 : 2;
     }
-    if (L.mode == kModeCheck) {
+    if (L.mode == kModeCheck || L.mode == kModeInPlaceFirst) {
         long long blocks = (L.count + kBlockThreads - 1) / kBlockThreads;
         if (blocks > L.blocks) blocks = L.blocks;
         if (blocks < 1) blocks = 1;

@@ -109,38 +109,54 @@ __device__ __forceinline__ void bits_to_flags(uint32_t bits8, uint32_t &lo, uint
     hi = spread4((bits8 >> 4) & 0xFu) << 7;
 }
 
-// Nonzero iff some unit of the U vectors is a surrogate.
+// Per-lane flags of a warp chunk of U vectors (two words per vector: units
+// 0..3 and 4..7).  chunk_surrogates() fills `a` with the gathered high bytes
+// and `b` with the surrogate flags; chunk_classes() turns them, in place,
+// into high-surrogate flags (`a`) and low-surrogate flags (`b`).
 template <int U>
-__device__ __forceinline__ uint32_t any_surrogate(const uint4 (&v)[U]) {
+struct ChunkBits {
+    uint32_t a[2 * U];
+    uint32_t b[2 * U];
+};
+
+// Returns nonzero iff some unit of the chunk's U vectors is a surrogate.
+template <int U>
+__device__ __forceinline__ uint32_t chunk_surrogates(const uint4 (&v)[U], ChunkBits<U> &cb) {
     uint32_t acc = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        uint32_t lo, hi;
-        high_bytes(v[u], lo, hi);
-        // (x - 0x01..) & ~x & 0x80.. is nonzero exactly when x has a zero byte.
-        const uint32_t x0 = (lo & 0xF8F8F8F8u) ^ 0xD8D8D8D8u;
-        const uint32_t x1 = (hi & 0xF8F8F8F8u) ^ 0xD8D8D8D8u;
-        acc |= ((x0 - 0x01010101u) & ~x0) | ((x1 - 0x01010101u) & ~x1);
+        cb.a[2 * u] = prmt(v[u].x, v[u].y, 0x7531);
+        cb.a[2 * u + 1] = prmt(v[u].z, v[u].w, 0x7531);
+        cb.b[2 * u] = surrogate_flags(cb.a[2 * u]);
+        cb.b[2 * u + 1] = surrogate_flags(cb.a[2 * u + 1]);
+        acc |= cb.b[2 * u] | cb.b[2 * u + 1];
     }
-    return acc & kFlagBits;
+    return acc;
 }
 
-// Cross-lane neighbour bits of a warp chunk: bit u of `from_prev` is set when
-// the unit just before this lane's vector u is a high surrogate, bit u of
-// `from_next` when the unit just after it is a low surrogate.  That unit is
-// the last (first) unit of the adjacent lane's vector, or for lane 0 (31) the
-// last unit of lane 31's vector in the previous slice (lane 0's in the next
-// slice), or the halo unit just outside the chunk:
+// High / low flags in place, and the cross-lane neighbour bits: bit u of
+// `from_prev` is set when the unit just before this lane's vector u is a high
+// surrogate, bit u of `from_next` when the unit just after it is a low
+// surrogate.  That unit is the last (first) unit of the adjacent lane's
+// vector, or for lane 0 (31) the last unit of lane 31's vector in the previous
+// slice (lane 0's in the next slice), or the halo unit just outside the chunk:
 //   halo_prev   lane 0: the unit before the chunk is a high surrogate
 //   halo_next   lane 31: the unit after the chunk is a low surrogate
 template <int U>
-__device__ __forceinline__ void neighbour_bits(const uint4 (&v)[U], uint32_t halo_prev, uint32_t halo_next, int lane,
-                                               uint32_t &from_prev, uint32_t &from_next) {
+__device__ __forceinline__ void chunk_classes(ChunkBits<U> &cb, uint32_t halo_prev, uint32_t halo_next, int lane,
+                                              uint32_t &from_prev, uint32_t &from_next) {
+#pragma unroll
+    for (int i = 0; i < 2 * U; ++i) {
+        const uint32_t lowhalf = low_half_flags(cb.a[i]);
+        const uint32_t sur = cb.b[i];
+        cb.a[i] = sur & ~lowhalf;
+        cb.b[i] = sur & lowhalf;
+    }
     uint32_t last_h = 0, first_l = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        last_h |= (uint32_t)unit_is_high(v[u].w >> 16) << u;
-        first_l |= (uint32_t)unit_is_low(v[u].x & 0xFFFFu) << u;
+        last_h |= (cb.a[2 * u + 1] >> 31) << u;
+        first_l |= ((cb.b[2 * u] >> 7) & 1u) << u;
     }
     from_prev = __shfl_sync(kFull, last_h, (lane + 31) & 31);
     from_next = __shfl_sync(kFull, first_l, (lane + 1) & 31);
@@ -148,25 +164,25 @@ __device__ __forceinline__ void neighbour_bits(const uint4 (&v)[U], uint32_t hal
     if (lane == 31) from_next = (from_next >> 1) | ((halo_next & 1u) << (U - 1));
 }
 
-// Mismatch flags of one vector (Section 1 rule, Section 3.1 step three).
-//   prev_h   1 if the unit before the vector is a high surrogate
-//   next_l   1 if the unit after the vector is a low surrogate
-//   st_lo/hi byte-lane flags of units that start a string (no left
-//            neighbour); st_next: the unit after the vector starts one.
-//            All zero for a single string.
-__device__ __forceinline__ void vec_mismatch(const uint4 &v, uint32_t prev_h, uint32_t next_l, uint32_t st_lo,
-                                             uint32_t st_hi, uint32_t st_next, uint32_t &bad_lo, uint32_t &bad_hi) {
-    uint32_t lo, hi;
-    high_bytes(v, lo, hi);
-    const uint32_t s_lo = surrogate_flags(lo), s_hi = surrogate_flags(hi);
-    const uint32_t b_lo = low_half_flags(lo), b_hi = low_half_flags(hi);
-    const uint32_t h_lo = s_lo & ~b_lo, h_hi = s_hi & ~b_hi;
-    const uint32_t l_lo = s_lo & b_lo, l_hi = s_hi & b_hi;
+// Mismatch flags of vector u of the chunk (Section 1 rule, Section 3.1 step
+// three): a high surrogate whose right neighbour is not low, or a low one
+// whose left neighbour is not high.
+//   st_lo/hi  byte-lane flags of units that start a string (no left
+//             neighbour); st_next: bit 0 set when the unit after the vector
+//             starts one.  Zero for a single string.
+template <int U>
+__device__ __forceinline__ void vec_bad(const ChunkBits<U> &cb, int u, uint32_t from_prev, uint32_t from_next,
+                                        uint32_t st_lo, uint32_t st_hi, uint32_t st_next, uint32_t &bad_lo,
+                                        uint32_t &bad_hi) {
+    const uint32_t h_lo = cb.a[2 * u], h_hi = cb.a[2 * u + 1];
+    const uint32_t l_lo = cb.b[2 * u], l_hi = cb.b[2 * u + 1];
+    const uint32_t pin = (from_prev << (31 - u)) & 0x80000000u;  // left neighbour of unit 0, at bit 31
+    const uint32_t nin = (from_next >> u) << 7;                   // right neighbour of unit 7, at bit 7
     // flag of unit k-1 / unit k+1 at bit 8k+7
-    const uint32_t ph_lo = __funnelshift_l(prev_h << 31, h_lo, 8) & ~st_lo;
+    const uint32_t ph_lo = __funnelshift_l(pin, h_lo, 8) & ~st_lo;
     const uint32_t ph_hi = __funnelshift_l(h_lo, h_hi, 8) & ~st_hi;
     const uint32_t nl_lo = __funnelshift_r(l_lo, l_hi, 8) & ~__funnelshift_r(st_lo, st_hi, 8);
-    const uint32_t nl_hi = __funnelshift_r(l_hi, next_l << 7, 8) & ~__funnelshift_r(st_hi, st_next << 7, 8);
+    const uint32_t nl_hi = __funnelshift_r(l_hi, nin, 8) & ~__funnelshift_r(st_hi, st_next << 7, 8);
     bad_lo = (h_lo & ~nl_lo) | (l_lo & ~ph_lo);
     bad_hi = (h_hi & ~nl_hi) | (l_hi & ~ph_hi);
 }

@@ -16,6 +16,7 @@ enum Mode : int {
     kModeOut = 0,      // out-of-place repair
     kModeInPlace = 1,  // in-place repair, stores only changed 16-byte blocks
     kModeCheck = 2,    // read-only first-error index
+    kModeInPlaceFirst = 3,  // batches only: in-place repair plus per-string first-error index
 };
 
 // How the single-string kernels bring data in.
@@ -50,7 +51,7 @@ struct BatchLaunch {
     uint16_t *out = nullptr;
     const long long *offsets = nullptr;
     long long count = 0;
-    long long *first_bad = nullptr;  // kModeCheck only
+    long long *first_bad = nullptr;  // kModeCheck and kModeInPlaceFirst
     int mode = kModeOut;
     int units_per_thread = 4;
     bool prefetch = false;

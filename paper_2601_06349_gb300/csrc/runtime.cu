@@ -120,13 +120,13 @@ int get_ctx(DeviceCtx **out) {
     }
     cudaStreamDestroy(s);
     utf16_config d;
-    d.single_variant = env_int("UTF16WF_SINGLE_VARIANT", kVariantTma);
+    d.single_variant = env_int("UTF16WF_SINGLE_VARIANT", kVariantLdg);
     d.single_units_per_thread = env_int("UTF16WF_SINGLE_U", 4);
     d.single_blocks_per_sm = env_int("UTF16WF_SINGLE_BLOCKS_PER_SM", 0);
     d.batch_units_per_thread = env_int("UTF16WF_BATCH_U", 4);
-    d.batch_prefetch = env_int("UTF16WF_BATCH_PREFETCH", 0);
+    d.batch_prefetch = env_int("UTF16WF_BATCH_PREFETCH", 1);
     d.batch_blocks_per_sm = env_int("UTF16WF_BATCH_BLOCKS_PER_SM", 0);
-    if (!config_valid(d)) d = utf16_config{kVariantTma, 4, 0, 4, 0, 0};
+    if (!config_valid(d)) d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);
@@ -259,6 +259,7 @@ const char *utf16_strerror(int code) {
         case UTF16_ECLOSED: return "the serving engine is shut down";
         case UTF16_EAGAIN: return "nothing ready yet";
         case UTF16_ETOOBIG: return "input longer than the no-allocation entry point accepts (2^40 units)";
+        case UTF16_ECANCELED: return "the request was cancelled before admission";
         default: return "unknown status code";
     }
 }

@@ -1,0 +1,557 @@
+// Serving engine: continuous batching of UTF-16 repair requests.
+//
+// Requests (one host string each) arrive at any time through
+// utf16_server_submit.  A scheduler thread takes whatever has arrived, admits
+// requests in arrival order against the device arena (a FIFO ring over one
+// allocation of the HBM budget) and launches them as one ragged batch as soon
+// as an in-flight batch slot is free: there is no waiting for a batch to fill.
+// Each batch moves through three streams, ordered by events:
+//   H2D stream      small requests packed in the slot's pinned staging buffer
+//                   (one copy, together with the offsets), large requests
+//                   copied straight from the caller's buffer;
+//   compute stream  in-place batch repair with per-string first-error index
+//                   (one persistent kernel, plus the lengths initialisation);
+//   D2H stream      the packed region and the first-error indices back to the
+//                   staging buffer, large requests straight to the caller.
+// While one batch computes, the next one's input is already on its way and
+// the previous one's output is coming back.  A completion thread waits for
+// batches in launch order, scatters small results to the callers' buffers,
+// records completion time and frees the ring space and the slot, which lets
+// the scheduler admit more requests.
+//
+// The kernels are the same ragged-batch kernels as utf16_*_batch, so a
+// request's result does not depend on which batch it lands in: every string
+// end is a hard boundary.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/utf16wf.h"
+#include "internal.h"
+#include "runtime.h"
+
+namespace u16wf {
+
+static int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// FIFO ring allocator over [0, cap): allocations are freed in the order they
+// were made, so the live region is one run (or two, once it wraps).
+class FifoRing {
+   public:
+    explicit FifoRing(int64_t cap) : cap_(cap) {}
+    int64_t alloc(int64_t size) {
+        if (size <= 0 || size > cap_) return -1;
+        int64_t off;
+        if (live_.empty()) {
+            off = 0;
+        } else {
+            const int64_t oldest = live_.front().first;
+            const int64_t newest_end = live_.back().first + live_.back().second;
+            if (live_.back().first >= oldest) {  // live: [oldest, newest_end)
+                if (cap_ - newest_end >= size)
+                    off = newest_end;
+                else if (oldest >= size)
+                    off = 0;
+                else
+                    return -1;
+            } else {  // wrapped: live [oldest, cap) and [0, newest_end)
+                if (oldest - newest_end >= size)
+                    off = newest_end;
+                else
+                    return -1;
+            }
+        }
+        live_.push_back({off, size});
+        used_ += size;
+        return off;
+    }
+    bool free_oldest() {
+        if (live_.empty()) return false;
+        used_ -= live_.front().second;
+        live_.pop_front();
+        return true;
+    }
+    int64_t used() const { return used_; }
+    int64_t live() const { return (int64_t)live_.size(); }
+    int64_t cap() const { return cap_; }
+
+   private:
+    int64_t cap_;
+    int64_t used_ = 0;
+    std::deque<std::pair<int64_t, int64_t>> live_;
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    const uint16_t *in = nullptr;
+    uint16_t *out = nullptr;
+    int64_t n = 0;
+    int64_t arrival_ns = 0;
+    int64_t done_ns = 0;
+    int64_t first_bad = -1;
+    int status = UTF16_OK;
+    bool large = false;
+    int64_t dev_off = 0;  // unit offset inside the batch
+};
+
+struct BatchSlot {
+    std::vector<Request> reqs;
+    int64_t ring_off = -1;
+    uint16_t *d_units = nullptr;
+    long long *d_offsets = nullptr;
+    long long *d_first = nullptr;
+    char *h_stage = nullptr;  // pinned: [offsets][first][small units]
+    int64_t h_cap = 0;
+    int64_t small_units = 0;
+    int64_t total_units = 0;
+    int64_t head_bytes = 0;  // offsets + first-error region, 256-aligned (same on device and host)
+    int64_t first_off = 0;   // byte offset of the first-error array in that region
+    int64_t strings = 0;     // strings of the launched batch (requests plus padding strings)
+    std::vector<int> req_of_string;  // request index of each string, -1 for padding
+    cudaEvent_t ev_h2d = nullptr, ev_kernel = nullptr, ev_done = nullptr;
+    int status = UTF16_OK;
+};
+
+// Head layout of a batch of up to `reqs` requests (at most 2*reqs strings:
+// a padding string may precede each aligned large request): offsets, then
+// first-error indices, each 256-byte aligned.
+static void batch_head_layout(int64_t reqs, int64_t &first_off, int64_t &head_bytes) {
+    first_off = align_up((2 * reqs + 2) * 8, 256);
+    head_bytes = first_off + align_up(2 * reqs * 8, 256);
+}
+
+}  // namespace u16wf
+
+struct utf16_server {
+    utf16_server_options opt;
+    int device = 0;
+    u16wf::DeviceCtx *ctx = nullptr;
+    char *arena = nullptr;
+    std::unique_ptr<u16wf::FifoRing> ring;
+    cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+    std::vector<u16wf::BatchSlot> slots;
+
+    std::mutex mu;
+    std::condition_variable cv_sched;  // new requests, freed slots / ring space, shutdown
+    std::condition_variable cv_done;   // completions available
+    std::deque<u16wf::Request> pending;
+    std::deque<int> free_slots;
+    std::deque<int> inflight;  // slot indices in launch order
+    std::deque<u16wf::Request> completed;
+    std::condition_variable cv_inflight;
+    bool stopping = false;
+    uint64_t next_ticket = 1;
+    int64_t submitted = 0, finished = 0;
+    utf16_server_stats stats;
+    std::thread scheduler, completer;
+};
+
+namespace u16wf {
+
+static void complete_request(utf16_server *S, Request &r, int status) {
+    r.status = status;
+    r.done_ns = now_ns();
+    S->completed.push_back(r);
+    S->finished++;
+}
+
+// Build and launch one batch on slot `si` from the admitted requests in it.
+// Small requests are packed first (staged through pinned memory), then the
+// large ones, each at a 16-byte aligned unit offset so that its own copies
+// are aligned; a gap before a large request is a padding string of its own,
+// so every request is exactly one string of the ragged batch.
+static void launch_batch_slot(utf16_server *S, int si) {
+    BatchSlot &b = S->slots[(size_t)si];
+    std::stable_partition(b.reqs.begin(), b.reqs.end(), [](const Request &r) { return !r.large; });
+    int64_t *h_off = (int64_t *)b.h_stage;
+    int64_t *h_first = (int64_t *)(b.h_stage + b.first_off);
+    uint16_t *h_units = (uint16_t *)(b.h_stage + b.head_bytes);
+    int64_t pos = 0;
+    int64_t strings = 0;
+    b.req_of_string.clear();
+    h_off[0] = 0;
+    for (int i = 0; i < (int)b.reqs.size(); ++i) {
+        Request &r = b.reqs[(size_t)i];
+        if (!r.large) {
+            memcpy(h_units + pos, r.in, (size_t)r.n * 2u);
+        } else if (pos % 8 != 0) {
+            pos = align_up(pos, 8);
+            h_off[++strings] = pos;  // padding string
+            b.req_of_string.push_back(-1);
+        }
+        if (!r.large) b.small_units = pos + r.n;
+        r.dev_off = pos;
+        pos += r.n;
+        h_off[++strings] = pos;
+        b.req_of_string.push_back(i);
+    }
+    b.total_units = pos;
+    b.strings = strings;
+    b.status = UTF16_OK;
+
+    cudaError_t e = cudaMemcpyAsync(b.d_offsets, h_off, (size_t)(strings + 1) * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, S->s_h2d);
+    if (e == cudaSuccess && b.small_units)
+        e = cudaMemcpyAsync(b.d_units, h_units, (size_t)b.small_units * 2u, cudaMemcpyHostToDevice, S->s_h2d);
+    for (const Request &r : b.reqs)
+        if (e == cudaSuccess && r.large)
+            e = cudaMemcpyAsync(b.d_units + r.dev_off, r.in, (size_t)r.n * 2u, cudaMemcpyHostToDevice, S->s_h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(b.ev_h2d, S->s_h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_comp, b.ev_h2d, 0);
+    if (e == cudaSuccess) {
+        BatchLaunch L;
+        L.in = b.d_units;
+        L.out = b.d_units;
+        L.offsets = b.d_offsets;
+        L.count = strings;
+        L.first_bad = b.d_first;
+        L.mode = kModeInPlaceFirst;
+        configure_batch(S->ctx, S->ctx->batch_config(b.total_units, strings), L);
+        e = launch_batch(L, S->s_comp);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b.ev_kernel, S->s_comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_d2h, b.ev_kernel, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_first, b.d_first, (size_t)strings * sizeof(int64_t), cudaMemcpyDeviceToHost, S->s_d2h);
+    if (e == cudaSuccess && b.small_units)
+        e = cudaMemcpyAsync(h_units, b.d_units, (size_t)b.small_units * 2u, cudaMemcpyDeviceToHost, S->s_d2h);
+    for (const Request &r : b.reqs)
+        if (e == cudaSuccess && r.large)
+            e = cudaMemcpyAsync(r.out, b.d_units + r.dev_off, (size_t)r.n * 2u, cudaMemcpyDeviceToHost, S->s_d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(b.ev_done, S->s_d2h);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.status = UTF16_ECUDA;
+    }
+}
+
+static void scheduler_main(utf16_server *S) {
+    cudaSetDevice(S->device);
+    const utf16_server_options &o = S->opt;
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        S->cv_sched.wait(lk, [&] { return S->stopping || (!S->pending.empty() && !S->free_slots.empty()); });
+        if (S->stopping) break;
+        const int si = S->free_slots.front();
+        BatchSlot &b = S->slots[(size_t)si];
+        b.reqs.clear();
+        // Admission in arrival order: stop at the first request that does not
+        // fit (keeps FIFO order; a later, smaller request does not overtake).
+        int64_t nreq = 0, small_units = 0, units = 0, bytes = 0, need = 0;
+        int64_t first_off = 0, head = 0;
+        while (!S->pending.empty()) {
+            Request &r = S->pending.front();
+            if (o.inject_fail_mod > 0 && (int64_t)(r.ticket % (uint64_t)o.inject_fail_mod) == o.inject_fail_mod - 1) {
+                // Host-side fault injection: this request's admission fails.
+                Request x = r;
+                S->pending.pop_front();
+                complete_request(S, x, UTF16_ENOMEM);
+                S->stats.rejected++;
+                S->cv_done.notify_all();
+                continue;
+            }
+            const bool large = r.n * 2 >= o.small_request_bytes;
+            const int64_t u2 = (large ? align_up(units, 8) : units) + r.n;
+            const int64_t sm2 = small_units + (large ? 0 : r.n);
+            int64_t f2, h2;
+            batch_head_layout(nreq + 1, f2, h2);
+            const int64_t need2 = h2 + align_up(u2 * 2, 256);
+            if (2 * (nreq + 1) > o.max_batch_strings || bytes + r.n * 2 > o.max_batch_bytes ||
+                h2 + sm2 * 2 > b.h_cap || need2 > S->ring->cap())
+                break;
+            nreq += 1;
+            units = u2;
+            small_units = sm2;
+            bytes += r.n * 2;
+            need = need2;
+            first_off = f2;
+            head = h2;
+            r.large = large;
+            b.reqs.push_back(r);
+            S->pending.pop_front();
+        }
+        if (b.reqs.empty()) continue;
+        // Reserve arena space; wait for completions while it does not fit.
+        int64_t ring_off;
+        while ((ring_off = S->ring->alloc(need)) < 0) {
+            if (S->inflight.empty() || S->stopping) break;
+            S->cv_sched.wait(lk);
+        }
+        if (ring_off < 0) {
+            for (Request &r : b.reqs) complete_request(S, r, S->stopping ? UTF16_ECLOSED : UTF16_ENOMEM);
+            b.reqs.clear();
+            S->cv_done.notify_all();
+            if (S->stopping) break;
+            continue;
+        }
+        S->free_slots.pop_front();
+        b.ring_off = ring_off;
+        b.first_off = first_off;
+        b.head_bytes = head;
+        b.small_units = 0;
+        char *base = S->arena + ring_off;
+        b.d_offsets = (long long *)base;
+        b.d_first = (long long *)(base + first_off);
+        b.d_units = (uint16_t *)(base + head);
+        S->stats.batches++;
+        S->stats.max_batch_requests = std::max(S->stats.max_batch_requests, nreq);
+        lk.unlock();
+        launch_batch_slot(S, si);
+        lk.lock();
+        S->inflight.push_back(si);
+        S->cv_inflight.notify_all();
+    }
+    // Shutdown: whatever is still pending is closed.
+    while (!S->pending.empty()) {
+        Request x = S->pending.front();
+        S->pending.pop_front();
+        complete_request(S, x, UTF16_ECLOSED);
+    }
+    S->cv_done.notify_all();
+}
+
+static void completer_main(utf16_server *S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        S->cv_inflight.wait(lk, [&] { return !S->inflight.empty() || S->stopping; });
+        if (S->inflight.empty() && S->stopping) break;
+        const int si = S->inflight.front();
+        BatchSlot &b = S->slots[(size_t)si];
+        lk.unlock();
+        int status = b.status;
+        if (status == UTF16_OK && cudaEventSynchronize(b.ev_done) != cudaSuccess) {
+            cudaGetLastError();
+            status = UTF16_ECUDA;
+        }
+        const int64_t *h_first = (const int64_t *)(b.h_stage + b.first_off);
+        const uint16_t *h_units = (const uint16_t *)(b.h_stage + b.head_bytes);
+        for (int64_t s = 0; s < b.strings; ++s) {
+            const int ri = b.req_of_string[(size_t)s];
+            if (ri < 0) continue;
+            Request &r = b.reqs[(size_t)ri];
+            if (status == UTF16_OK && !r.large) memcpy(r.out, h_units + r.dev_off, (size_t)r.n * 2u);
+            r.first_bad = h_first[s];
+        }
+        const int64_t t_done = now_ns();
+        lk.lock();
+        for (Request &r : b.reqs) {
+            r.status = status;
+            r.done_ns = std::max(t_done, now_ns());
+            S->completed.push_back(r);
+            S->finished++;
+            S->stats.completed++;
+            S->stats.units += r.n;
+        }
+        b.reqs.clear();
+        S->ring->free_oldest();
+        S->inflight.pop_front();
+        S->free_slots.push_back(si);
+        S->cv_sched.notify_all();
+        S->cv_done.notify_all();
+    }
+}
+
+}  // namespace u16wf
+
+using namespace u16wf;
+
+extern "C" {
+
+int utf16_server_default_options(utf16_server_options *o) {
+    if (!o) return UTF16_EINVAL;
+    o->hbm_budget_bytes = 4LL << 30;
+    o->max_batch_strings = 1 << 16;
+    o->max_batch_bytes = 256LL << 20;
+    o->max_inflight_batches = 4;
+    o->staging_bytes = 64LL << 20;
+    o->small_request_bytes = 256LL << 10;
+    o->inject_fail_mod = 0;
+    return UTF16_OK;
+}
+
+int utf16_server_create(const utf16_server_options *opt, utf16_server **out) {
+    if (!opt || !out) return UTF16_EINVAL;
+    const utf16_server_options &o = *opt;
+    if (o.hbm_budget_bytes < (1 << 20) || o.max_batch_strings < 2 || o.max_batch_bytes < 1024 ||
+        o.max_inflight_batches < 1 || o.max_inflight_batches > 64 || o.staging_bytes < 4096 ||
+        o.small_request_bytes < 0 || o.inject_fail_mod < 0)
+        return UTF16_EINVAL;
+    std::unique_ptr<utf16_server> S(new utf16_server());
+    S->opt = o;
+    memset(&S->stats, 0, sizeof(S->stats));
+    if (cudaGetDevice(&S->device) != cudaSuccess) return UTF16_ECUDA;
+    int rc = get_ctx(&S->ctx);
+    if (rc) return rc;
+    if (cudaMalloc((void **)&S->arena, (size_t)o.hbm_budget_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ENOMEM;
+    }
+    S->ring.reset(new FifoRing(o.hbm_budget_bytes));
+    if (cudaStreamCreateWithFlags(&S->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->s_d2h, cudaStreamNonBlocking) != cudaSuccess)
+        return UTF16_ECUDA;
+    S->slots.resize((size_t)o.max_inflight_batches);
+    for (int i = 0; i < o.max_inflight_batches; ++i) {
+        BatchSlot &b = S->slots[(size_t)i];
+        b.h_cap = o.staging_bytes;
+        if (cudaHostAlloc((void **)&b.h_stage, (size_t)b.h_cap, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ENOMEM;
+        }
+        if (cudaEventCreateWithFlags(&b.ev_h2d, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.ev_kernel, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming) != cudaSuccess)
+            return UTF16_ECUDA;
+        S->free_slots.push_back(i);
+    }
+    utf16_server *raw = S.release();
+    raw->scheduler = std::thread(scheduler_main, raw);
+    raw->completer = std::thread(completer_main, raw);
+    *out = raw;
+    return UTF16_OK;
+}
+
+int64_t utf16_server_clock_ns(void) { return now_ns(); }
+
+int utf16_server_submit(utf16_server *S, const uint16_t *host_in, uint16_t *host_out, int64_t n, int64_t arrival_ns,
+                        uint64_t *ticket) {
+    if (!S || n < 0 || (n > 0 && (!host_in || !host_out))) return UTF16_EINVAL;
+    // Every request must fit an otherwise empty arena and staging buffer.
+    const int64_t need = 1024 + align_up(n * 2, 256) + 512;
+    const bool large = n * 2 >= S->opt.small_request_bytes;
+    if (need > S->opt.hbm_budget_bytes || n * 2 > S->opt.max_batch_bytes ||
+        (!large && n * 2 + 1024 > S->opt.staging_bytes))
+        return UTF16_ENOMEM;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stopping) return UTF16_ECLOSED;
+    Request r;
+    r.ticket = S->next_ticket++;
+    r.in = host_in;
+    r.out = host_out;
+    r.n = n;
+    r.arrival_ns = arrival_ns > 0 ? arrival_ns : now_ns();
+    if (n == 0) {
+        r.first_bad = 0;
+        complete_request(S, r, UTF16_OK);
+        S->submitted++;
+        S->cv_done.notify_all();
+    } else {
+        S->pending.push_back(r);
+        S->submitted++;
+        S->cv_sched.notify_all();
+    }
+    if (ticket) *ticket = r.ticket;
+    return UTF16_OK;
+}
+
+int utf16_server_cancel(utf16_server *S, uint64_t ticket) {
+    if (!S) return UTF16_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto it = S->pending.begin(); it != S->pending.end(); ++it)
+        if (it->ticket == ticket) {
+            Request x = *it;
+            S->pending.erase(it);
+            complete_request(S, x, UTF16_ECANCELED);
+            S->cv_done.notify_all();
+            return UTF16_OK;
+        }
+    return UTF16_EAGAIN;  // already admitted (or unknown): it will complete normally
+}
+
+int utf16_server_next(utf16_server *S, utf16_completion *c, int64_t timeout_us) {
+    if (!S || !c) return UTF16_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto ready = [&] { return !S->completed.empty(); };
+    if (timeout_us == 0) {
+        if (!ready()) return UTF16_EAGAIN;
+    } else {
+        const int64_t t = timeout_us < 0 ? (int64_t)3600 * 1000000 : timeout_us;
+        if (!S->cv_done.wait_for(lk, std::chrono::microseconds(t), ready)) return UTF16_ETIMEOUT;
+    }
+    const Request r = S->completed.front();
+    S->completed.pop_front();
+    c->ticket = r.ticket;
+    c->first_bad = r.first_bad;
+    c->status = r.status;
+    c->n = r.n;
+    c->arrival_ns = r.arrival_ns;
+    c->done_ns = r.done_ns;
+    return UTF16_OK;
+}
+
+int utf16_server_stats_get(utf16_server *S, utf16_server_stats *st) {
+    if (!S || !st) return UTF16_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *st = S->stats;
+    st->pending = (int64_t)S->pending.size();
+    st->inflight_batches = (int64_t)S->inflight.size();
+    st->arena_used_bytes = S->ring->used();
+    return UTF16_OK;
+}
+
+int utf16_server_destroy(utf16_server *S) {
+    if (!S) return UTF16_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+        S->cv_sched.notify_all();
+        S->cv_inflight.notify_all();
+    }
+    if (S->scheduler.joinable()) S->scheduler.join();
+    if (S->completer.joinable()) S->completer.join();
+    cudaStreamSynchronize(S->s_h2d);
+    cudaStreamSynchronize(S->s_comp);
+    cudaStreamSynchronize(S->s_d2h);
+    for (BatchSlot &b : S->slots) {
+        if (b.h_stage) cudaFreeHost(b.h_stage);
+        if (b.ev_h2d) cudaEventDestroy(b.ev_h2d);
+        if (b.ev_kernel) cudaEventDestroy(b.ev_kernel);
+        if (b.ev_done) cudaEventDestroy(b.ev_done);
+    }
+    if (S->arena) cudaFree(S->arena);
+    cudaStreamDestroy(S->s_h2d);
+    cudaStreamDestroy(S->s_comp);
+    cudaStreamDestroy(S->s_d2h);
+    cudaGetLastError();
+    delete S;
+    return UTF16_OK;
+}
+
+// ---------------------------------------------------------------- FIFO ring
+struct utf16_arena {
+    FifoRing ring;
+    explicit utf16_arena(int64_t cap) : ring(cap) {}
+};
+
+int utf16_arena_create(int64_t capacity, utf16_arena **out) {
+    if (capacity <= 0 || !out) return UTF16_EINVAL;
+    *out = new utf16_arena(capacity);
+    return UTF16_OK;
+}
+int64_t utf16_arena_alloc(utf16_arena *a, int64_t size) { return a ? a->ring.alloc(size) : -1; }
+int utf16_arena_free_oldest(utf16_arena *a) { return (a && a->ring.free_oldest()) ? UTF16_OK : UTF16_EINVAL; }
+int64_t utf16_arena_used(const utf16_arena *a) { return a ? a->ring.used() : -1; }
+int utf16_arena_destroy(utf16_arena *a) {
+    delete a;
+    return UTF16_OK;
+}
+
+}  // extern "C"

@@ -37,16 +37,13 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
     long long my_first = LLONG_MAX;
-    auto halo = [&](long long p) { return unit_at(A, p); };
 
     if constexpr (PF) {
-        uint4 nv[U];
+        Chunk<U> nv;
         long long c = gwarp;
         if (c < A.chunks) load_chunk<MODE, U>(A, vin, c, lane, nv);
         while (c < A.chunks) {
-            uint4 v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = nv[u];
+            const Chunk<U> v = nv;
             const long long cur = c;
             c += nwarps;
             unsigned long long g = ~0ull;
@@ -60,7 +57,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
                 g = __shfl_sync(kFull, g, 0);
                 if (g != ~0ull && (long long)g < cfirst) break;
             }
-            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first, halo);
+            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first);
         }
     } else {
         for (long long c = gwarp; c < A.chunks; c += nwarps) {
@@ -69,13 +66,13 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
             if constexpr (MODE == kModeCheck) {
                 if (lane == 0) g = *((volatile unsigned long long *)&A.slot->min);
             }
-            uint4 v[U];
+            Chunk<U> v;
             load_chunk<MODE, U>(A, vin, c, lane, v);
             if constexpr (MODE == kModeCheck) {
                 g = __shfl_sync(kFull, g, 0);
                 if (g != ~0ull && (long long)g < cfirst) break;
             }
-            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first, halo);
+            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first);
         }
     }
 

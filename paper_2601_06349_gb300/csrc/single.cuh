@@ -32,10 +32,18 @@ __device__ __forceinline__ uint32_t unit_at(const SingleArgs &A, long long p) {
     return 0u;
 }
 
+// A loaded warp chunk: this lane's U vectors, and (lanes 0 and 31) the units
+// just before and after the chunk, which the slow path needs as neighbours.
+template <int U>
+struct Chunk {
+    uint4 v[U];
+    uint32_t halo;
+};
+
 // Load warp chunk c: 128-bit loads inside the string, unit loads at its ends.
 template <int MODE, int U>
 __device__ __forceinline__ void load_chunk(const SingleArgs &A, const uint4 *vin, long long c, int lane,
-                                           uint4 (&v)[U]) {
+                                           Chunk<U> &ch) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     const long long cfirst = c * CU - A.a;
     if (cfirst >= 0 && cfirst + CU <= A.n) {
@@ -43,19 +51,22 @@ __device__ __forceinline__ void load_chunk(const SingleArgs &A, const uint4 *vin
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if constexpr (MODE == kModeInPlace)
-                v[u] = ld_plain(p + 32 * u);
+                ch.v[u] = ld_plain(p + 32 * u);
             else
-                v[u] = ld_stream(p + 32 * u);
+                ch.v[u] = ld_stream(p + 32 * u);
         }
     } else {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
-            v[u] = make_uint4(0, 0, 0, 0);
+            ch.v[u] = make_uint4(0, 0, 0, 0);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) vec_set_unit(v[u], k, unit_at(A, p0 + k));
+            for (int k = 0; k < 8; ++k) vec_set_unit(ch.v[u], k, unit_at(A, p0 + k));
         }
     }
+    ch.halo = 0;
+    if (lane == 0) ch.halo = unit_at(A, cfirst - 1);
+    if (lane == 31) ch.halo = unit_at(A, cfirst + CU);
 }
 
 // Units of vector u of this lane that lie in [0, n), as an 8-bit mask.
@@ -66,74 +77,73 @@ __device__ __forceinline__ uint32_t valid_bits8(long long p0, long long n) {
     return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
 }
 
-// Steps 2-5 of the chunk starting at unit cfirst whose vectors are in v.
-// `halo(p)` returns unit p for the two units just outside the chunk.
-template <int MODE, bool FB, int ST, int U, class Halo>
-__device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfirst, const uint4 (&v)[U], int lane,
-                                              long long &my_first, Halo halo) {
+// Store vector u of a chunk (dst = this lane's first unit of the chunk).
+template <int MODE, int ST>
+__device__ __forceinline__ void store_chunk_vec(uint16_t *dst, int u, const uint4 &f, bool edge, long long p0,
+                                                long long n, uint32_t bad8) {
+    uint16_t *d = dst + u * kWarpSliceUnits;
+    if (!edge) {
+        if constexpr (MODE == kModeInPlace)
+            *reinterpret_cast<uint4 *>(d) = f;
+        else
+            store_vec<ST>(d, f);
+    } else {
+        const uint32_t w8 = (MODE == kModeInPlace) ? bad8 : valid_bits8(p0, n);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (w8 & (1u << k)) d[k] = (uint16_t)vec_unit(f, k);
+    }
+}
+
+// Steps 2-5 of the chunk starting at unit cfirst.
+template <int MODE, bool FB, int ST, int U>
+__device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfirst, const Chunk<U> &ch, int lane,
+                                              long long &my_first) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     const bool edge = (cfirst < 0) || (cfirst + CU > A.n);
-    const uint32_t surr = any_surrogate<U>(v);
+    const long long lfirst = cfirst + lane * kUnitsPerVec;  // this lane's first unit
+    uint16_t *dst = (MODE == kModeCheck) ? nullptr : A.out + lfirst;
+    ChunkBits<U> cb;
+    const uint32_t surr = chunk_surrogates<U>(ch.v, cb);
 
     if (!__any_sync(kFull, surr != 0)) {
         // Well-formed chunk: copy out of place, nothing otherwise.
         if constexpr (MODE == kModeOut) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
-                if (!edge) {
-                    store_vec<ST>(A.out + p0, v[u]);
-                } else {
-                    const uint32_t w8 = valid_bits8(p0, A.n);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (w8 & (1u << k)) A.out[p0 + k] = (uint16_t)vec_unit(v[u], k);
-                }
-            }
+            for (int u = 0; u < U; ++u) store_chunk_vec<MODE, ST>(dst, u, ch.v[u], edge, lfirst + u * kWarpSliceUnits, A.n, 0u);
         }
         return;
     }
 
-    // Slow path: locate the mismatched units, one vector at a time.
-    uint32_t hp = 0, hn = 0;
-    if (lane == 0) hp = unit_is_high(halo(cfirst - 1));
-    if (lane == 31) hn = unit_is_low(halo(cfirst + CU));
+    // Slow path: locate the mismatched units.
     uint32_t from_prev, from_next;
-    neighbour_bits<U>(v, hp, hn, lane, from_prev, from_next);
+    chunk_classes<U>(cb, unit_is_high(ch.halo), unit_is_low(ch.halo), lane, from_prev, from_next);
     bool found = false;
     uint32_t any_bad = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
+        const long long p0 = lfirst + u * kWarpSliceUnits;
         uint32_t bad_lo, bad_hi;
-        vec_mismatch(v[u], (from_prev >> u) & 1u, (from_next >> u) & 1u, 0u, 0u, 0u, bad_lo, bad_hi);
+        vec_bad<U>(cb, u, from_prev, from_next, 0u, 0u, 0u, bad_lo, bad_hi);
         if (edge) {
             uint32_t vlo, vhi;
             bits_to_flags(valid_bits8(p0, A.n), vlo, vhi);
             bad_lo &= vlo;
             bad_hi &= vhi;
         }
-        const bool vb = (bad_lo | bad_hi) != 0;
-        any_bad |= bad_lo | bad_hi;
-        if constexpr (MODE != kModeCheck) {
-            if (MODE == kModeOut || vb) {
-                const uint4 f = vb ? fix_vec(v[u], bad_lo, bad_hi) : v[u];
-                if (!edge) {
-                    if constexpr (MODE == kModeInPlace)
-                        *reinterpret_cast<uint4 *>(A.out + p0) = f;
-                    else
-                        store_vec<ST>(A.out + p0, f);
-                } else {
-                    const uint32_t w8 = (MODE == kModeInPlace) ? (gather4(bad_lo) | (gather4(bad_hi) << 4))
-                                                               : valid_bits8(p0, A.n);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (w8 & (1u << k)) A.out[p0 + k] = (uint16_t)vec_unit(f, k);
-                }
-            }
+        const uint32_t vbad = bad_lo | bad_hi;
+        any_bad |= vbad;
+        if constexpr (MODE == kModeOut) {
+            uint4 f = ch.v[u];
+            if (vbad) f = fix_vec(f, bad_lo, bad_hi);
+            store_chunk_vec<MODE, ST>(dst, u, f, edge, p0, A.n, 0u);
+        } else if constexpr (MODE == kModeInPlace) {
+            if (vbad)
+                store_chunk_vec<MODE, ST>(dst, u, fix_vec(ch.v[u], bad_lo, bad_hi), edge, p0, A.n,
+                                          gather4(bad_lo) | (gather4(bad_hi) << 4));
         }
         if constexpr (FB) {
-            if (vb && !found) {
+            if (vbad && !found) {
                 found = true;
                 const long long p = p0 + first_flag(bad_lo, bad_hi);
                 my_first = p < my_first ? p : my_first;

@@ -138,15 +138,14 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
     // Chunks at the ends of the string, with 128-bit and unit loads, while
     // the first copies are in flight.
     {
-        auto halo = [&](long long p) { return unit_at(A, p); };
         const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
         const long long n_lo = T.edge_chunks_lo, n_hi = A.chunks - T.edge_chunks_hi;
         for (long long e = gwarp; e < n_lo + n_hi; e += nwarps) {
             const long long c = e < n_lo ? e : T.edge_chunks_hi + (e - n_lo);
-            uint4 v[kTmaU];
-            load_chunk<MODE, kTmaU>(A, vin, c, lane, v);
-            process_chunk<MODE, FB, 16, kTmaU>(A, c * (kTmaU * kWarpSliceUnits) - A.a, v, lane, my_first, halo);
+            Chunk<kTmaU> ch;
+            load_chunk<MODE, kTmaU>(A, vin, c, lane, ch);
+            process_chunk<MODE, FB, 16, kTmaU>(A, c * (kTmaU * kWarpSliceUnits) - A.a, ch, lane, my_first);
         }
     }
 
@@ -154,12 +153,16 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
         if (k >= s_issued) break;  // copies stopped early (first error already known)
         const int s = (int)(k % kTmaStages);
         const unsigned parity = (unsigned)((k / kTmaStages) & 1);
-        if (!mbar_wait_bounded(&full[s], parity)) {
+        // One thread polls; the others wait at the barrier and then observe
+        // the completed phase themselves (one try_wait each, which acquires
+        // the copied bytes).
+        if (threadIdx.x == 0 && !mbar_wait_bounded(&full[s], parity)) {
             atomicExch(&g_tma_timeout, 1u);
             s_fault = 1;
         }
         __syncthreads();
         if (s_fault) break;
+        if (!mbar_try_wait(&full[s], parity) && !mbar_wait_bounded(&full[s], parity)) atomicExch(&g_tma_timeout, 1u);
         const long long t = first_tile + k * gridDim.x;
         const long long tile_first = t * kTileUnits - A.a;
         const uint4 *stage = stages + (size_t)s * kStageVecs;
@@ -170,12 +173,16 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
             skip = (g != ~0ull && (long long)g < tile_first);
         }
         if (!skip) {
-            uint4 v[kTmaU];
+            Chunk<kTmaU> ch;
 #pragma unroll
-            for (int u = 0; u < kTmaU; ++u) v[u] = stage[1 + warp * (32 * kTmaU) + u * 32 + lane];
+            for (int u = 0; u < kTmaU; ++u) ch.v[u] = stage[1 + warp * (32 * kTmaU) + u * 32 + lane];
+            // units just outside this warp's chunk, from the stage (tile halo at the tile ends)
+            const int r = warp * (kTmaU * kWarpSliceUnits) + kUnitsPerVec;
+            ch.halo = 0;
+            if (lane == 0) ch.halo = stage_units[r - 1];
+            if (lane == 31) ch.halo = stage_units[r + kTmaU * kWarpSliceUnits];
             const long long cfirst = tile_first + (long long)warp * (kTmaU * kWarpSliceUnits);
-            auto halo = [&](long long p) { return (uint32_t)stage_units[p - tile_first + kUnitsPerVec]; };
-            process_chunk<MODE, FB, 16, kTmaU>(A, cfirst, v, lane, my_first, halo);
+            process_chunk<MODE, FB, 16, kTmaU>(A, cfirst, ch, lane, my_first);
         }
         __syncthreads();  // every warp is done with stage s
         if (threadIdx.x == 0) {

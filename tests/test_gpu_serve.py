@@ -1,0 +1,156 @@
+"""Serving engine (continuous batching) against the oracle, through the C ABI:
+every request's result and first-error index equal the oracle's, the same
+alone and in a mix under load; small budgets force admission to wait for
+completions; host-injected admission failures and cancellations leave every
+other request exact; the plain per-request replay agrees too."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2601_06349_gb300 as p
+    p.init_device()
+    return p
+
+
+def _requests(count, seed, big=True):
+    rng = np.random.default_rng(seed)
+    lens = workloads.request_lengths(count, seed=seed)
+    if not big:
+        lens = np.minimum(lens, 70_000)
+    lens[::97] = 0  # a few empty requests
+    reqs = []
+    for i, n in enumerate(lens):
+        u = workloads.mixed(int(n), 1e-3, seed=seed * 100_003 + i)
+        if n > 2 and rng.random() < 0.3:
+            u[0] = 0xDC00  # starts with a low surrogate
+        if n > 2 and rng.random() < 0.3:
+            u[-1] = 0xD800  # ends with a high surrogate
+        reqs.append(u)
+    return reqs
+
+
+def _expect(reqs):
+    return [(oracle.to_well_formed(u), oracle.first_bad(u)) for u in reqs]
+
+
+def test_submit_next_matches_oracle(pkg):
+    reqs = _requests(300, 11)
+    want = _expect(reqs)
+    outs = [np.zeros_like(u) for u in reqs]
+    with pkg.Server(hbm_budget_bytes=96 << 20, max_inflight_batches=3, small_request_bytes=64 << 10,
+                    staging_bytes=16 << 20, max_batch_bytes=64 << 20) as srv:
+        tickets = {srv.submit(u, o): i for i, (u, o) in enumerate(zip(reqs, outs))}
+        got = {}
+        while len(got) < len(reqs):
+            c = srv.next(timeout_us=30_000_000)
+            assert c is not None, "timed out waiting for completions"
+            got[tickets[c["ticket"]]] = c
+        st = srv.stats()
+    for i, (w, fb) in enumerate(want):
+        assert got[i]["status"] == 0
+        assert got[i]["first_bad"] == fb, i
+        assert np.array_equal(outs[i], w), i
+    assert st["batches"] >= 2
+
+
+def test_same_alone_and_in_the_mix(pkg):
+    reqs = _requests(400, 12)
+    want = _expect(reqs)
+    alone = [np.zeros_like(u) for u in reqs]
+    alone_fb = []
+    with pkg.Server(hbm_budget_bytes=512 << 20) as srv:
+        for u, o in zip(reqs, alone):  # one at a time: each request is a batch of its own
+            srv.submit(u, o)
+            c = srv.next(timeout_us=30_000_000)
+            assert c is not None and c["status"] == 0
+            alone_fb.append(c["first_bad"])
+        mix = [np.zeros_like(u) for u in reqs]
+        lat, fb = srv.replay(reqs, mix, rate_per_s=50_000, seed=3)  # arrivals overlap: batched together
+        st = srv.stats()
+    assert st["max_batch_requests"] > 1, "the mix never formed a multi-request batch"
+    for i, (w, f) in enumerate(want):
+        assert np.array_equal(alone[i], w) and alone_fb[i] == f, i
+        assert np.array_equal(mix[i], alone[i]) and fb[i] == alone_fb[i], i
+    assert np.all(lat > 0)
+
+
+def test_pinned_host_buffers(pkg):
+    import torch
+    reqs = _requests(120, 13)
+    want = _expect(reqs)
+    ins = [torch.from_numpy(u.view(np.int16)).pin_memory() for u in reqs]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    with pkg.Server(small_request_bytes=32 << 10) as srv:
+        lat, fb = srv.replay(ins, outs, rate_per_s=0, seed=4)
+    for i, (w, f) in enumerate(want):
+        assert np.array_equal(outs[i].numpy().view(np.uint16), w) and fb[i] == f, i
+
+
+def test_injected_admission_failures_leave_others_exact(pkg):
+    reqs = _requests(200, 14, big=False)
+    want = _expect(reqs)
+    outs = [np.full_like(u, 0x5A5A) for u in reqs]
+    with pkg.Server(inject_fail_mod=7) as srv:
+        tickets = [srv.submit(u, o) for u, o in zip(reqs, outs)]
+        res = {}
+        while len(res) < len(reqs):
+            c = srv.next(timeout_us=30_000_000)
+            assert c is not None
+            res[c["ticket"]] = c
+    failed = 0
+    for i, t in enumerate(tickets):
+        c = res[t]
+        if reqs[i].size and t % 7 == 6:
+            assert c["status"] == pkg.ENOMEM
+            assert np.all(outs[i] == 0x5A5A)  # untouched
+            failed += 1
+        else:
+            assert c["status"] == 0 and c["first_bad"] == want[i][1], i
+            assert np.array_equal(outs[i], want[i][0]), i
+    assert failed > 10
+
+
+def test_cancel_before_admission(pkg):
+    reqs = _requests(400, 15, big=False)
+    want = _expect(reqs)
+    outs = [np.zeros_like(u) for u in reqs]
+    with pkg.Server(max_inflight_batches=1, max_batch_strings=8) as srv:
+        tickets = [srv.submit(u, o) for u, o in zip(reqs, outs)]
+        cancelled = {t for t in tickets[200:] if srv.cancel(t)}
+        res = {}
+        while len(res) < len(reqs):
+            c = srv.next(timeout_us=30_000_000)
+            assert c is not None
+            res[c["ticket"]] = c
+    assert cancelled, "nothing was still pending to cancel"
+    for i, t in enumerate(tickets):
+        if t in cancelled:
+            assert res[t]["status"] == pkg.ECANCELED
+        else:
+            assert res[t]["status"] == 0 and res[t]["first_bad"] == want[i][1]
+            assert np.array_equal(outs[i], want[i][0]), i
+
+
+def test_plain_replay_matches(pkg):
+    reqs = _requests(150, 16)
+    want = _expect(reqs)
+    outs = [np.zeros_like(u) for u in reqs]
+    lat, fb = pkg.plain_replay(reqs, outs, rate_per_s=0, seed=5)
+    for i, (w, f) in enumerate(want):
+        assert np.array_equal(outs[i], w) and fb[i] == f, i
+
+
+def test_oversize_request_rejected(pkg):
+    with pkg.Server(hbm_budget_bytes=1 << 20, max_batch_bytes=1 << 19) as srv:
+        big = np.zeros(1 << 20, np.uint16)
+        with pytest.raises(pkg.Utf16Error):
+            srv.submit(big, big)
