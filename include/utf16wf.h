@@ -176,13 +176,13 @@ int utf16_to_well_formed_first_bad_noalloc(const uint16_t *in, uint16_t *out, in
 typedef struct {
     int single_variant;          /* 0: 128-bit loads; 1: 128-bit loads, next chunk requested before the
                                     current one is processed; 2: TMA bulk copies into a 4-stage
-                                    shared-memory ring (16 KiB tiles), repair only: the
-                                    read-only check then uses variant 0 */
+                                    shared-memory ring (16 KiB tiles); repair forms only */
     int single_units_per_thread; /* 16-byte vectors per thread per warp chunk: 2 or 4 (TMA uses 4) */
     int single_blocks_per_sm;    /* persistent grid = SMs x this; 0 = as many as fit */
     int batch_units_per_thread;  /* 2 or 4 */
     int batch_prefetch;          /* 0 or 1 */
     int batch_blocks_per_sm;     /* 0 = as many as fit */
+    int check_variant;           /* read-only check (utf16_is_well_formed): 0, 1 or 2 as single_variant */
 } utf16_config;
 
 /* Default configuration of the current device (used where nothing is tuned). */

@@ -100,6 +100,37 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             }
         }
     }
+    // The read-only check separately: each data path with the winner's other settings.
+    float best_check = 1e30f;
+    for (int variant = 0; variant <= 2; ++variant) {
+        utf16_config c = winner;
+        c.check_variant = variant;
+        SingleLaunch L;
+        L.in = in;
+        L.n = n;
+        L.mode = kModeCheck;
+        L.first_bad = true;
+        configure_single(ctx, c, L);
+        L.slot = slot;
+        L.result = &slot->result;
+        if (launch_single(L, t.s) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+        cudaEventRecord(t.a, t.s);
+        for (int r = 0; r < reps; ++r) launch_single(L, t.s);
+        cudaEventRecord(t.b, t.s);
+        if (cudaEventSynchronize(t.b) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        if (ms < best_check) {
+            best_check = ms;
+            winner.check_variant = variant;
+        }
+    }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         const int b = bucket_of(n);

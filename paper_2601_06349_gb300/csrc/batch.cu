@@ -124,10 +124,19 @@ __device__ __forceinline__ void batch_store_vec(uint16_t *d, const uint4 &f, boo
     }
 }
 
+// Per-warp shared scratch of the slow path.
+template <int U>
+struct WarpScratch {
+    uint32_t bits[U * kWarpSliceUnits / 32 + 1];  // string starts in [cfirst, cfirst + CU]; the last bit marks one just past
+    uint32_t prefix[32];                          // starts in words 0..w-1 of `bits` (first-error modes)
+    long long window[33];                         // offsets[s_first - 1 .. s_first + 31]
+};
+
 template <int MODE, int ST, int U>
 __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long long cfirst, long long lo, long long hi,
-                                                    const BatchChunk<U> &ch, int lane, uint32_t *bits,
+                                                    const BatchChunk<U> &ch, int lane, WarpScratch<U> &ws,
                                                     long long &hint) {
+    uint32_t *bits = ws.bits;
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     constexpr int kWords = (int)(CU / 32) + 1;
     const bool edge = (cfirst < lo) || (cfirst + CU > hi);
@@ -152,6 +161,9 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
     const long long s_first = lower_bound_warp(A.offsets, A.count, hint, cfirst, lane);
     hint = s_first;
     long long s_last = s_first - 1;  // last string index starting in the chunk
+    // A chunk with at most 31 starts and no empty string (no two equal
+    // offsets) finds the string of a unit by counting starts before it.
+    bool simple = true;
     for (long long base = s_first;; base += 32) {
         const long long idx = base + lane;
         const long long off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
@@ -162,6 +174,15 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
         }
         const unsigned m = __ballot_sync(kFull, inside);
         s_last = base + __popc(m) - 1 > s_last ? base + __popc(m) - 1 : s_last;
+        if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
+            if (base == s_first) {
+                ws.window[lane + 1] = off;
+                const long long next = __shfl_down_sync(kFull, off, 1);
+                const bool dup = inside && lane < 31 && next == off;
+                simple = (m != kFull) && !__any_sync(kFull, dup);
+                if (lane == 0) ws.window[0] = s_first > 0 ? A.offsets[s_first - 1] : LLONG_MIN;
+            }
+        }
         if (m != kFull) break;
     }
     __syncwarp();
@@ -170,6 +191,21 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
     chunk_classes<U>(cb, unit_is_high(ch.halo), unit_is_low(ch.halo), lane, from_prev, from_next);
     long long prev_s = -1;
     const long long s_lo = hint > 0 ? hint - 1 : 0;
+    if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
+        if (simple) {
+            // prefix[w] = number of starts in words 0 .. w-1
+            constexpr int kChunkWords = U * kWarpSliceUnits / 32;
+            const uint32_t c = lane < kChunkWords ? __popc(bits[lane]) : 0u;
+            uint32_t incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, d);
+                if (lane >= d) incl += t;
+            }
+            ws.prefix[lane] = incl - c;
+            __syncwarp();
+        }
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int r0 = u * kWarpSliceUnits + lane * kUnitsPerVec;
@@ -205,18 +241,31 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
                 const int b = __ffs(rest) - 1;
                 rest &= rest - 1;
                 const long long p = p0 + b;
-                long long a_i = s_lo, b_i = s_last > s_lo ? s_last : s_lo;
-                while (a_i < b_i) {  // largest index with offsets[index] <= p
-                    const long long mid = (a_i + b_i + 1) >> 1;
-                    if (A.offsets[mid] <= p)
-                        a_i = mid;
-                    else
-                        b_i = mid - 1;
+                long long a_i, start;
+                if (simple) {
+                    // starts at or before p inside the chunk, all distinct
+                    const int r = r0 + b;
+                    const int k = (int)ws.prefix[r >> 5] + __popc(bits[r >> 5] & (0xFFFFFFFFu >> (31 - (r & 31))));
+                    a_i = s_first - 1 + k;
+                    start = ws.window[k];
+                } else {
+                    a_i = s_lo;
+                    long long b_i = s_last > s_lo ? s_last : s_lo;
+                    while (a_i < b_i) {  // largest index with offsets[index] <= p
+                        const long long mid = (a_i + b_i + 1) >> 1;
+                        if (A.offsets[mid] <= p)
+                            a_i = mid;
+                        else
+                            b_i = mid - 1;
+                    }
+                    start = -1;
                 }
-                a_i = a_i < A.count - 1 ? a_i : A.count - 1;
+                if (a_i > A.count - 1) a_i = A.count - 1;
+                if (a_i < 0) a_i = 0;
                 if (a_i != prev_s) {
                     prev_s = a_i;
-                    atomicMin(&A.first_bad[a_i], p - A.offsets[a_i]);
+                    if (start < 0 || start == LLONG_MIN) start = A.offsets[a_i];
+                    atomicMin(&A.first_bad[a_i], p - start);
                 }
             }
         }
@@ -225,11 +274,10 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
 
 template <int MODE, int ST, int U, bool PF>
 __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A) {
-    constexpr int kWords = U * kWarpSliceUnits / 32 + 1;  // bit CU marks a start just past the chunk
-    __shared__ uint32_t s_bits[kBlockThreads / 32][kWords];
+    __shared__ WarpScratch<U> s_scratch[kBlockThreads / 32];
 
     const int lane = threadIdx.x & 31;
-    uint32_t *bits = s_bits[threadIdx.x >> 5];
+    WarpScratch<U> &bits = s_scratch[threadIdx.x >> 5];
 
     const long long lo = A.offsets[0];
     const long long hi = A.offsets[A.count];

@@ -79,7 +79,7 @@ utf16_config DeviceCtx::batch_config(int64_t units, int64_t count) {
 }
 
 static bool config_valid(const utf16_config &c) {
-    return c.single_variant >= 0 && c.single_variant <= 2 &&
+    return c.single_variant >= 0 && c.single_variant <= 2 && c.check_variant >= 0 && c.check_variant <= 2 &&
            (c.single_units_per_thread == 2 || c.single_units_per_thread == 4) && c.single_blocks_per_sm >= 0 &&
            c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
            (c.batch_prefetch == 0 || c.batch_prefetch == 1) && c.batch_blocks_per_sm >= 0 &&
@@ -126,7 +126,8 @@ int get_ctx(DeviceCtx **out) {
     d.batch_units_per_thread = env_int("UTF16WF_BATCH_U", 4);
     d.batch_prefetch = env_int("UTF16WF_BATCH_PREFETCH", 1);
     d.batch_blocks_per_sm = env_int("UTF16WF_BATCH_BLOCKS_PER_SM", 0);
-    if (!config_valid(d)) d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0};
+    d.check_variant = env_int("UTF16WF_CHECK_VARIANT", kVariantLdg);
+    if (!config_valid(d)) d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);
@@ -134,10 +135,7 @@ int get_ctx(DeviceCtx **out) {
 }
 
 void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) {
-    L.variant = cfg.single_variant;
-    // The read-only check streams 2 bytes per unit and measured faster with
-    // 128-bit loads than through the shared-memory ring on GB300.
-    if (L.mode == kModeCheck && L.variant == kVariantTma) L.variant = kVariantLdg;
+    L.variant = L.mode == kModeCheck ? cfg.check_variant : cfg.single_variant;
     L.units_per_thread = cfg.single_units_per_thread;
     const bool fb = L.first_bad || L.mode == kModeCheck;
     const bool tma = L.variant == kVariantTma;

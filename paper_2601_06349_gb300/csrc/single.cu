@@ -126,7 +126,6 @@ SingleArgs make_single_args(const SingleLaunch &L, int units_per_chunk) {
 }
 
 cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream) {
-    if (L.variant == kVariantTma && L.mode != kModeOut) return launch_single_tma(L, stream);
     if (L.variant == kVariantTma && store_width(L) == 16) return launch_single_tma(L, stream);
     const int U = L.units_per_thread == 2 ? 2 : 4;
     const bool pf = L.variant == kVariantLdgPrefetch;
