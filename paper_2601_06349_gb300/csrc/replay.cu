@@ -89,7 +89,7 @@ extern "C" int utf16_server_replay(utf16_server *S, const uint16_t *const *input
         while (true) {
             if (!submitting.load() && (int64_t)done.size() >= submitted_ok.load()) break;
             utf16_completion c;
-            const int r = utf16_server_next(S, &c, 100000);
+            const int r = utf16_server_next(S, &c, 2000);
             if (r == UTF16_OK) done.push_back(c);
             else if (r != UTF16_ETIMEOUT && r != UTF16_EAGAIN) break;
         }
