@@ -127,24 +127,29 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = ["single.cu", "single.cuh", "device.cuh", "internal.h"]
+
+
+def kernel_source_hash(files=KERNEL_SOURCES):
+    """Hash of the sources that define the single-string kernels."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2601_06349_gb300", "csrc", "*"))):
+    for name in sorted(files):
+        p = os.path.join(ROOT, "paper_2601_06349_gb300", "csrc", name)
         with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode())
+            h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(name):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    """DRAM bytes per launch from the committed ncu record, if it was taken
+    on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[name]
-        if e.get("kernel_hash") != kernel_source_hash():
+        if e.get("kernel_hash") != kernel_source_hash(e.get("sources", KERNEL_SOURCES)):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
