@@ -214,6 +214,15 @@ int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int64_t *offse
  */
 int utf16_check_device_errors(void);
 
+/*
+ * Self-test of the kernels' bounded waits: one GPU thread waits on a barrier
+ * that nothing completes, with the TMA kernel's wait routine and a limit of
+ * `limit_ns` (1 .. 2e9).  Returns UTF16_ETIMEOUT when the wait gave up as it
+ * must (and the device-error flag is then set, as after a real timeout);
+ * synchronous.  Nothing faults and nothing hangs: the wait is bounded.
+ */
+int utf16_selftest_bounded_wait(int64_t limit_ns);
+
 /* ===================================================================== *
  * Serving: continuous batching of repair requests (host strings).
  *

@@ -84,6 +84,7 @@ def _declare(lib):
         "utf16_autotune_single": ([vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_autotune_batch": ([vp, vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_check_device_errors": ([], ctypes.c_int),
+        "utf16_selftest_bounded_wait": ([i64], ctypes.c_int),
         "utf16_to_well_formed_first_bad_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "utf16_release_device": ([], ctypes.c_int),
         "utf16_server_default_options": ([ctypes.POINTER(ServerOptions)], ctypes.c_int),

@@ -45,6 +45,7 @@ const void *single_kernel_for_occupancy(int mode, bool fb, int u, int variant = 
 size_t single_tma_smem_bytes();
 cudaError_t prepare_single_tma();
 unsigned int read_and_clear_tma_timeout();
+int run_bounded_wait_probe(long long limit_ns);  // 1: the wait gave up, 0: it completed, -1: CUDA error
 
 struct BatchLaunch {
     const uint16_t *in = nullptr;

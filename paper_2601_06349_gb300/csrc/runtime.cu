@@ -324,6 +324,16 @@ int utf16_set_config(const utf16_config *cfg) {
     return UTF16_OK;
 }
 
+int utf16_selftest_bounded_wait(int64_t limit_ns) {
+    if (limit_ns <= 0 || limit_ns > 2000000000LL) return UTF16_EINVAL;
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    const int r = run_bounded_wait_probe(limit_ns);
+    if (r < 0) return UTF16_ECUDA;
+    return r ? UTF16_ETIMEOUT : UTF16_OK;
+}
+
 int utf16_check_device_errors(void) {
     if (cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();

@@ -71,15 +71,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait for phase `parity` of `bar`: false after 2^22 polls or 1 s.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+// Bounded wait for phase `parity` of `bar`: false after 2^22 polls or
+// `limit_ns` nanoseconds (1 s by default).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  unsigned long long limit_ns = 1000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned i = 0; i < (1u << 22); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 255u && global_ns() - t0 > 1000000000ull) return false;
+        if ((i & 255u) == 255u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
+}
+
+// Self-test of the bounded wait: one thread waits on a barrier that nothing
+// completes; the wait must give up, record the timeout like the TMA kernel
+// does, and return.
+__global__ void bounded_wait_probe(unsigned long long limit_ns, unsigned int *gave_up) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const bool done = mbar_wait_bounded(&bar, 0, limit_ns);
+        *gave_up = done ? 0u : 1u;
+        if (!done) atomicExch(&g_tma_timeout, 1u);
+    }
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
@@ -262,6 +278,23 @@ cudaError_t prepare_single_tma() {
         }
     }
     return cudaSuccess;
+}
+
+int run_bounded_wait_probe(long long limit_ns) {
+    unsigned int *d = nullptr, h = 0;
+    if (cudaMalloc((void **)&d, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    bounded_wait_probe<<<1, 32>>>((unsigned long long)limit_ns, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int)h;
 }
 
 unsigned int read_and_clear_tma_timeout() {

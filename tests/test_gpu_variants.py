@@ -104,3 +104,21 @@ def test_autotuner_choice_is_correct(pkg):
     got = to_host(pkg.to_well_formed_batch(du, do))
     assert np.array_equal(got, oracle.to_well_formed_batch(units, offs))
     pkg.check_device_errors()
+
+
+def test_bounded_wait_gives_up_and_reports(pkg):
+    """A wait on a barrier that nothing completes gives up after its limit
+    (here 50 ms) and raises the device-error flag that the host reads; the
+    context stays usable."""
+    import time
+    lib = pkg.lib()
+    pkg.check_device_errors()  # start clean
+    t0 = time.perf_counter()
+    assert lib.utf16_selftest_bounded_wait(50_000_000) == pkg.ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert lib.utf16_check_device_errors() == pkg.ETIMEOUT
+    assert lib.utf16_check_device_errors() == 0  # read and cleared
+    # the device still works
+    u = workloads.mixed(100_000, 1e-2, seed=5)
+    d = to_dev(u)
+    assert pkg.first_error_index_sync(d) == oracle.first_bad(u)
