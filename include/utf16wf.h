@@ -111,6 +111,19 @@ int utf16_to_well_formed_first_bad(const uint16_t *in, uint16_t *out, int64_t n,
 int utf16_is_well_formed(const uint16_t *in, int64_t n, int64_t *first_bad, utf16_stream_t stream);
 
 /*
+ * Full error report: the index of every unit that toWellFormed replaces.
+ *   positions  [capacity] int64, DEVICE (may be NULL when capacity == 0):
+ *              receives min(count, capacity) distinct indices, in no
+ *              particular order (the GPU reserves room per warp with one
+ *              atomic); when count > capacity, which indices are kept is
+ *              unspecified.
+ *   count      one int64_t, device or host pointer: the total number of
+ *              mismatched units (host pointer: the call waits for the stream).
+ */
+int utf16_error_positions(const uint16_t *in, int64_t n, int64_t *positions, int64_t capacity, int64_t *count,
+                          utf16_stream_t stream);
+
+/*
  * Ragged batch forms.  String s is in[offsets[s] .. offsets[s+1]) for
  * s = 0 .. num_strings-1.
  *   offsets    [num_strings + 1] int64, DEVICE, non-decreasing, offsets[0] >= 0
@@ -183,6 +196,8 @@ typedef struct {
     int batch_prefetch;          /* 0 or 1 */
     int batch_blocks_per_sm;     /* 0 = as many as fit */
     int check_variant;           /* read-only check (utf16_is_well_formed): 0, 1 or 2 as single_variant */
+    int inplace_unit_stores;     /* in-place repair of single strings: 0 = store each 16-byte block that
+                                    holds a replaced unit, 1 = store only the replaced units (2 bytes) */
 } utf16_config;
 
 /* Default configuration of the current device (used where nothing is tuned). */

@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
     _fields_ = [("single_variant", ctypes.c_int), ("single_units_per_thread", ctypes.c_int),
                 ("single_blocks_per_sm", ctypes.c_int), ("batch_units_per_thread", ctypes.c_int),
                 ("batch_prefetch", ctypes.c_int), ("batch_blocks_per_sm", ctypes.c_int),
-                ("check_variant", ctypes.c_int)]
+                ("check_variant", ctypes.c_int), ("inplace_unit_stores", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -84,6 +84,7 @@ def _declare(lib):
         "utf16_autotune_single": ([vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_autotune_batch": ([vp, vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_check_device_errors": ([], ctypes.c_int),
+        "utf16_error_positions": ([vp, i64, vp, i64, vp, vp], ctypes.c_int),
         "utf16_selftest_bounded_wait": ([i64], ctypes.c_int),
         "utf16_to_well_formed_first_bad_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "utf16_release_device": ([], ctypes.c_int),
@@ -220,6 +221,22 @@ def first_error_index_sync(inp, *, stream=None) -> int:
         _check(lib().utf16_is_well_formed(inp.data_ptr(), inp.numel(), ctypes.addressof(v),
                                           _stream(stream, inp.device)), "utf16_is_well_formed")
     return v.value
+
+
+def error_positions(inp, capacity=None, *, stream=None):
+    """Indices of all mismatched units (unordered) as an int64 CUDA tensor of
+    length min(count, capacity), and the total count (the call waits)."""
+    torch = _torch()
+    _units(inp, "inp")
+    if capacity is None:
+        capacity = inp.numel()
+    pos = torch.empty(max(int(capacity), 1), dtype=torch.int64, device=inp.device)
+    cnt = ctypes.c_int64(-1)
+    with torch.cuda.device(inp.device):
+        _check(lib().utf16_error_positions(inp.data_ptr(), inp.numel(), pos.data_ptr(), int(capacity),
+                                           ctypes.addressof(cnt), _stream(stream, inp.device)),
+               "utf16_error_positions")
+    return pos[:min(cnt.value, int(capacity))], cnt.value
 
 
 def is_well_formed(inp, *, stream=None) -> bool:

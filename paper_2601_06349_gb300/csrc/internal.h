@@ -17,6 +17,7 @@ enum Mode : int {
     kModeInPlace = 1,  // in-place repair, stores only changed 16-byte blocks
     kModeCheck = 2,    // read-only first-error index
     kModeInPlaceFirst = 3,  // batches only: in-place repair plus per-string first-error index
+    kModeList = 4,          // single strings: positions of all mismatched units (unordered) and their count
 };
 
 // How the single-string kernels bring data in.
@@ -38,6 +39,9 @@ struct SingleLaunch {
     Slot *slot = nullptr;
     long long *result = nullptr;
     uint32_t lead = 0, trail = 0;  // outside neighbours (0 = none)
+    bool unit_stores = false;      // in place: 2-byte stores of the replaced units instead of 16-byte blocks
+    long long *positions = nullptr;  // kModeList: output array
+    long long capacity = 0;          // kModeList: its length
 };
 
 cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream);

@@ -80,6 +80,7 @@ utf16_config DeviceCtx::batch_config(int64_t units, int64_t count) {
 
 static bool config_valid(const utf16_config &c) {
     return c.single_variant >= 0 && c.single_variant <= 2 && c.check_variant >= 0 && c.check_variant <= 2 &&
+           (c.inplace_unit_stores == 0 || c.inplace_unit_stores == 1) &&
            (c.single_units_per_thread == 2 || c.single_units_per_thread == 4) && c.single_blocks_per_sm >= 0 &&
            c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
            (c.batch_prefetch == 0 || c.batch_prefetch == 1) && c.batch_blocks_per_sm >= 0 &&
@@ -127,7 +128,8 @@ int get_ctx(DeviceCtx **out) {
     d.batch_prefetch = env_int("UTF16WF_BATCH_PREFETCH", 1);
     d.batch_blocks_per_sm = env_int("UTF16WF_BATCH_BLOCKS_PER_SM", 0);
     d.check_variant = env_int("UTF16WF_CHECK_VARIANT", kVariantLdg);
-    if (!config_valid(d)) d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg};
+    d.inplace_unit_stores = env_int("UTF16WF_INPLACE_UNIT_STORES", 0);
+    if (!config_valid(d)) d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg, 0};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);
@@ -136,6 +138,9 @@ int get_ctx(DeviceCtx **out) {
 
 void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) {
     L.variant = L.mode == kModeCheck ? cfg.check_variant : cfg.single_variant;
+    L.unit_stores = L.mode == kModeInPlace && cfg.inplace_unit_stores != 0;
+    // Unit stores exist in the 128-bit-load kernels only.
+    if (L.unit_stores && L.variant == kVariantTma) L.variant = kVariantLdg;
     L.units_per_thread = cfg.single_units_per_thread;
     const bool fb = L.first_bad || L.mode == kModeCheck;
     const bool tma = L.variant == kVariantTma;
@@ -371,6 +376,44 @@ int utf16_is_well_formed(const uint16_t *in, int64_t n, int64_t *first_bad, utf1
     if (n == 0) return empty_first_bad(first_bad, (cudaStream_t)stream);
     if (!in || misaligned(in)) return UTF16_EINVAL;
     return run_single(in, nullptr, n, kModeCheck, first_bad, (cudaStream_t)stream, 0, 0);
+}
+
+int utf16_error_positions(const uint16_t *in, int64_t n, int64_t *positions, int64_t capacity, int64_t *count,
+                          utf16_stream_t stream) {
+    if (n < 0 || capacity < 0 || !count || (capacity > 0 && !positions)) return UTF16_EINVAL;
+    if (n == 0) return empty_first_bad(count, (cudaStream_t)stream);
+    if (!in || misaligned(in) || ((uintptr_t)positions & 7u)) return UTF16_EINVAL;
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool on_device = is_device_ptr(count);
+    Slot *slot = nullptr;
+    rc = ctx->slot_for(s, &slot);
+    if (rc) return rc;
+    SingleLaunch L;
+    L.in = in;
+    L.n = n;
+    L.mode = kModeList;
+    utf16_config cfg = ctx->single_config(n);
+    cfg.single_variant = cfg.single_variant == kVariantTma ? kVariantLdg : cfg.single_variant;
+    configure_single(ctx, cfg, L);
+    L.slot = slot;
+    L.result = on_device ? (long long *)count : &slot->result;
+    L.positions = (long long *)positions;
+    L.capacity = capacity;
+    if (launch_single(L, s) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    if (!on_device) {
+        if (cudaMemcpyAsync(count, &slot->result, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+    }
+    return UTF16_OK;
 }
 
 int utf16_to_well_formed_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t num_strings,

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
     }
 
     if constexpr (FB) finish_first_bad(A, my_first, lane);
+    if constexpr (MODE == kModeList) finish_list(A);
 }
 
 template <int MODE, bool FB, int ST>
@@ -95,6 +96,7 @@ static const void *single_kernel_ptr(int u, bool pf) {
 
 static const void *pick_single(int mode, bool fb, int st, int u, bool pf) {
     if (mode == kModeCheck) return single_kernel_ptr<kModeCheck, true, 16>(u, pf);
+    if (mode == kModeList) return single_kernel_ptr<kModeList, false, 16>(u, pf);
     if (mode == kModeInPlace)
         return fb ? single_kernel_ptr<kModeInPlace, true, 16>(u, pf) : single_kernel_ptr<kModeInPlace, false, 16>(u, pf);
     switch (st) {
@@ -122,15 +124,19 @@ SingleArgs make_single_args(const SingleLaunch &L, int units_per_chunk) {
     A.result = L.result;
     A.lead = L.lead;
     A.trail = L.trail;
+    A.unit_stores = L.unit_stores ? 1 : 0;
+    A.positions = L.positions;
+    A.capacity = L.capacity;
     return A;
 }
 
 cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream) {
-    if (L.variant == kVariantTma && store_width(L) == 16) return launch_single_tma(L, stream);
+    if (L.variant == kVariantTma && store_width(L) == 16 && L.mode != kModeList)
+        return launch_single_tma(L, stream);
     const int U = L.units_per_thread == 2 ? 2 : 4;
     const bool pf = L.variant == kVariantLdgPrefetch;
     const SingleArgs A = make_single_args(L, U * kWarpSliceUnits);
-    const bool fb = L.first_bad || L.mode == kModeCheck;
+    const bool fb = (L.first_bad || L.mode == kModeCheck) && L.mode != kModeList;
     const void *fn = pick_single(L.mode, fb, store_width(L), U, pf);
     const long long warps_per_block = kBlockThreads / 32;
     long long blocks = (A.chunks + warps_per_block - 1) / warps_per_block;
@@ -141,7 +147,7 @@ cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream) {
 }
 
 const void *single_kernel_for_occupancy(int mode, bool fb, int u, int variant) {
-    if (variant == kVariantTma) return single_tma_kernel_for_occupancy(mode, fb);
+    if (variant == kVariantTma && mode != kModeList) return single_tma_kernel_for_occupancy(mode, fb);
     return pick_single(mode, fb, 16, u == 2 ? 2 : 4, variant == kVariantLdgPrefetch);
 }
 

@@ -20,6 +20,9 @@ struct SingleArgs {
     int a;               // misalignment of `in` in units
     uint32_t lead;       // unit just before in[0] (0 = none); a chunk of a longer string passes its neighbour
     uint32_t trail;      // unit just after in[n-1] (0 = none)
+    int unit_stores;     // in place: store replaced units one by one (2 bytes) instead of their 16-byte block
+    long long *positions;  // list mode: positions of mismatched units (unordered), `capacity` entries
+    long long capacity;
 };
 
 SingleArgs make_single_args(const SingleLaunch &L, int units_per_chunk);
@@ -102,7 +105,7 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     const bool edge = (cfirst < 0) || (cfirst + CU > A.n);
     const long long lfirst = cfirst + lane * kUnitsPerVec;  // this lane's first unit
-    uint16_t *dst = (MODE == kModeCheck) ? nullptr : A.out + lfirst;
+    uint16_t *dst = (MODE == kModeCheck || MODE == kModeList) ? nullptr : A.out + lfirst;
     ChunkBits<U> cb;
     const uint32_t surr = chunk_surrogates<U>(ch.v, cb);
 
@@ -138,9 +141,44 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
             if (vbad) f = fix_vec(f, bad_lo, bad_hi);
             store_chunk_vec<MODE, ST>(dst, u, f, edge, p0, A.n, 0u);
         } else if constexpr (MODE == kModeInPlace) {
-            if (vbad)
-                store_chunk_vec<MODE, ST>(dst, u, fix_vec(ch.v[u], bad_lo, bad_hi), edge, p0, A.n,
-                                          gather4(bad_lo) | (gather4(bad_hi) << 4));
+            if (vbad) {
+                if (A.unit_stores) {
+                    uint32_t rest = gather4(bad_lo) | (gather4(bad_hi) << 4);
+                    uint16_t *d = dst + u * kWarpSliceUnits;
+                    while (rest) {
+                        d[__ffs(rest) - 1] = (uint16_t)0xFFFDu;
+                        rest &= rest - 1;
+                    }
+                } else {
+                    store_chunk_vec<MODE, ST>(dst, u, fix_vec(ch.v[u], bad_lo, bad_hi), edge, p0, A.n,
+                                              gather4(bad_lo) | (gather4(bad_hi) << 4));
+                }
+            }
+        } else if constexpr (MODE == kModeList) {
+            // All positions: reserve room for the warp's units with one atomic,
+            // then each lane writes its own (warp-aggregated, unordered).
+            const uint32_t bits8 = gather4(bad_lo) | (gather4(bad_hi) << 4);
+            const uint32_t mine = __popc(bits8);
+            uint32_t incl = mine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, d);
+                if (lane >= d) incl += t;
+            }
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            if (total) {
+                unsigned long long base = 0;
+                if (lane == 31) base = atomicAdd((unsigned long long *)&A.slot->pad1, (unsigned long long)total);
+                base = __shfl_sync(kFull, base, 31);
+                unsigned long long at = base + (incl - mine);
+                uint32_t rest = bits8;
+                while (rest) {
+                    const int k = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    if ((long long)at < A.capacity) A.positions[at] = p0 + k;
+                    ++at;
+                }
+            }
         }
         if constexpr (FB) {
             if (vbad && !found) {
@@ -181,6 +219,26 @@ __device__ __forceinline__ void finish_first_bad(const SingleArgs &A, long long 
         const unsigned long long g = atomicAdd(&A.slot->min, 0ull);
         *A.result = (g < (unsigned long long)A.n) ? (long long)g : A.n;
         A.slot->min = ~0ull;
+        A.slot->done = 0u;
+        __threadfence();
+    }
+}
+
+// List mode: the last block publishes the number of mismatched units and
+// resets the counter for the next launch.
+__device__ __forceinline__ void finish_list(const SingleArgs &A) {
+    __shared__ bool s_last_l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&A.slot->done, 1u);
+        s_last_l = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last_l && threadIdx.x == 0) {
+        __threadfence();
+        *A.result = (long long)atomicAdd((unsigned long long *)&A.slot->pad1, 0ull);
+        A.slot->pad1 = 0;
         A.slot->done = 0u;
         __threadfence();
     }
