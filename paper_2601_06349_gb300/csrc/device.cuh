@@ -134,9 +134,9 @@ __device__ __forceinline__ uint32_t chunk_surrogates(const uint4 (&v)[U], ChunkB
     return acc;
 }
 
-// High / low flags in place, and the cross-lane neighbour bits: bit u of
+// High / low flags in place, and the cross-lane neighbour flags: bit 8u+7 of
 // `from_prev` is set when the unit just before this lane's vector u is a high
-// surrogate, bit u of `from_next` when the unit just after it is a low
+// surrogate, bit 8u+7 of `from_next` when the unit just after it is a low
 // surrogate.  That unit is the last (first) unit of the adjacent lane's
 // vector, or for lane 0 (31) the last unit of lane 31's vector in the previous
 // slice (lane 0's in the next slice), or the halo unit just outside the chunk:
@@ -152,16 +152,25 @@ __device__ __forceinline__ void chunk_classes(ChunkBits<U> &cb, uint32_t halo_pr
         cb.a[i] = sur & ~lowhalf;
         cb.b[i] = sur & lowhalf;
     }
-    uint32_t last_h = 0, first_l = 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        last_h |= (cb.a[2 * u + 1] >> 31) << u;
-        first_l |= ((cb.b[2 * u] >> 7) & 1u) << u;
+    // Byte u of last_h: byte 3 of h_hi[u] (flag of unit 7 of vector u at its
+    // bit 7); byte u of first_l: byte 0 of l_lo[u] (flag of unit 0).
+    uint32_t last_h, first_l;
+    if constexpr (U == 4) {
+        last_h = prmt(prmt(cb.a[1], cb.a[3], 0x0073), prmt(cb.a[5], cb.a[7], 0x0073), 0x5410);
+        first_l = prmt(prmt(cb.b[0], cb.b[2], 0x0040), prmt(cb.b[4], cb.b[6], 0x0040), 0x5410);
+    } else if constexpr (U == 2) {
+        last_h = prmt(cb.a[1], cb.a[3], 0x0073) & 0xFFFFu;  // bytes 2, 3 are copies, not flags
+        first_l = prmt(cb.b[0], cb.b[2], 0x0040) & 0xFFFFu;
+    } else {
+        last_h = cb.a[2 * U - 1] >> 24;
+        first_l = cb.b[0] & 0xFFu;
     }
     from_prev = __shfl_sync(kFull, last_h, (lane + 31) & 31);
     from_next = __shfl_sync(kFull, first_l, (lane + 1) & 31);
-    if (lane == 0) from_prev = (from_prev << 1) | (halo_prev & 1u);
-    if (lane == 31) from_next = (from_next >> 1) | ((halo_next & 1u) << (U - 1));
+    // lane 0: vector u's left neighbour is lane 31's vector u-1; lane 31:
+    // vector u's right neighbour is lane 0's vector u+1; the halo at the ends.
+    if (lane == 0) from_prev = (from_prev << 8) | ((halo_prev & 1u) << 7);
+    if (lane == 31) from_next = (from_next >> 8) | ((halo_next & 1u) << (8 * U - 1));
 }
 
 // Mismatch flags of vector u of the chunk (Section 1 rule, Section 3.1 step
@@ -176,8 +185,9 @@ __device__ __forceinline__ void vec_bad(const ChunkBits<U> &cb, int u, uint32_t 
                                         uint32_t &bad_hi) {
     const uint32_t h_lo = cb.a[2 * u], h_hi = cb.a[2 * u + 1];
     const uint32_t l_lo = cb.b[2 * u], l_hi = cb.b[2 * u + 1];
-    const uint32_t pin = (from_prev << (31 - u)) & 0x80000000u;  // left neighbour of unit 0, at bit 31
-    const uint32_t nin = (from_next >> u) << 7;                   // right neighbour of unit 7, at bit 7
+    // from_prev / from_next hold one flag per vector at bit 8u+7
+    const uint32_t pin = (from_prev << (24 - 8 * u)) & 0x80000000u;  // left neighbour of unit 0, at bit 31
+    const uint32_t nin = (from_next >> (8 * u)) & 0x80u;              // right neighbour of unit 7, at bit 7
     // flag of unit k-1 / unit k+1 at bit 8k+7
     const uint32_t ph_lo = __funnelshift_l(pin, h_lo, 8) & ~st_lo;
     const uint32_t ph_hi = __funnelshift_l(h_lo, h_hi, 8) & ~st_hi;
