@@ -126,19 +126,17 @@ __device__ __forceinline__ void batch_store_vec(uint16_t *d, const uint4 &f, boo
 
 // Per-warp shared scratch of the slow path.
 template <int U>
-struct WarpScratch {
-    uint32_t bits[U * kWarpSliceUnits / 32 + 1];  // string starts in [cfirst, cfirst + CU]; the last bit marks one just past
-    uint32_t prefix[32];                          // starts in words 0..w-1 of `bits` (first-error modes)
-    long long window[33];                         // offsets[s_first - 1 .. s_first + 31]
+struct __align__(16) WarpScratch {
+    uint8_t starts[U * kWarpSliceUnits + 16];  // 0x80 at r when a string starts at unit cfirst + r (r <= CU)
+    long long win[32];                          // offsets[base .. base + 31]: the chunk's first window
+    long long win_prev;                         // offsets[base - 1], or LLONG_MIN
 };
 
 template <int MODE, int ST, int U>
 __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long long cfirst, long long lo, long long hi,
                                                     const BatchChunk<U> &ch, int lane, WarpScratch<U> &ws,
                                                     long long &hint) {
-    uint32_t *bits = ws.bits;
     constexpr long long CU = (long long)U * kWarpSliceUnits;
-    constexpr int kWords = (int)(CU / 32) + 1;
     const bool edge = (cfirst < lo) || (cfirst + CU > hi);
     const long long lfirst = cfirst + lane * kUnitsPerVec;
     uint16_t *dst = (MODE == kModeCheck) ? nullptr : A.out + lfirst;
@@ -155,68 +153,57 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
         return;
     }
 
-    // String starts in [cfirst, cfirst + CU].
-    for (int i = lane; i < kWords; i += 32) bits[i] = 0u;
-    __syncwarp();
-    const long long s_first = lower_bound_warp(A.offsets, A.count, hint, cfirst, lane);
+    // String starts in [cfirst, cfirst + CU] as a byte map (0x80 per start).
+    constexpr int kStartVecs = (int)(CU + 16) / 16;
+    for (int i = lane; i < kStartVecs; i += 32) reinterpret_cast<uint4 *>(ws.starts)[i] = make_uint4(0, 0, 0, 0);
+    const long long cend = cfirst + CU;
+    // One window of 32 offsets from the previous chunk's first string
+    // usually covers both the search and the collection.
+    long long base = hint;
+    long long idx = base + lane;
+    long long off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
+    unsigned ge = __ballot_sync(kFull, off >= cfirst);
+    if (ge == 0) {  // the chunk's strings start beyond this window: search
+        base = lower_bound_warp(A.offsets, A.count, base + 32, cfirst, lane);
+        idx = base + lane;
+        off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
+        ge = __ballot_sync(kFull, off >= cfirst);
+    }
+    const long long s_first = base + __ffs(ge) - 1;  // first string starting at or after cfirst
+    const long long base_first = base;                 // ws.win holds offsets[base_first ..]
     hint = s_first;
+    bool simple = true;  // all starts of the chunk lie in the first window
+    if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
+        ws.win[lane] = off;
+        if (lane == 0) ws.win_prev = base > 0 ? A.offsets[base - 1] : LLONG_MIN;
+    }
     long long s_last = s_first - 1;  // last string index starting in the chunk
-    // A chunk with at most 31 starts and no empty string (no two equal
-    // offsets) finds the string of a unit by counting starts before it.
-    bool simple = true;
-    for (long long base = s_first;; base += 32) {
-        const long long idx = base + lane;
-        const long long off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
-        const bool inside = off >= cfirst && off <= cfirst + CU;
-        if (inside) {
-            const long long r = off - cfirst;
-            atomicOr(&bits[r >> 5], 1u << (r & 31));
-        }
+    __syncwarp();
+    for (int w = 0;; ++w) {
+        const bool inside = off >= cfirst && off <= cend;
+        if (inside) ws.starts[off - cfirst] = 0x80;
         const unsigned m = __ballot_sync(kFull, inside);
-        s_last = base + __popc(m) - 1 > s_last ? base + __popc(m) - 1 : s_last;
-        if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
-            if (base == s_first) {
-                ws.window[lane + 1] = off;
-                const long long next = __shfl_down_sync(kFull, off, 1);
-                const bool dup = inside && lane < 31 && next == off;
-                simple = (m != kFull) && !__any_sync(kFull, dup);
-                if (lane == 0) ws.window[0] = s_first > 0 ? A.offsets[s_first - 1] : LLONG_MIN;
-            }
-        }
-        if (m != kFull) break;
+        if (m) s_last = base + 31 - __clz(m);
+        // continue while the window's last entry still starts inside the chunk
+        if (!(m >> 31)) break;
+        simple = false;
+        base += 32;
+        idx = base + lane;
+        off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
     }
     __syncwarp();
-
     uint32_t from_prev, from_next;
     chunk_classes<U>(cb, unit_is_high(ch.halo), unit_is_low(ch.halo), lane, from_prev, from_next);
     long long prev_s = -1;
     const long long s_lo = hint > 0 ? hint - 1 : 0;
-    if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
-        if (simple) {
-            // prefix[w] = number of starts in words 0 .. w-1
-            constexpr int kChunkWords = U * kWarpSliceUnits / 32;
-            const uint32_t c = lane < kChunkWords ? __popc(bits[lane]) : 0u;
-            uint32_t incl = c;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, incl, d);
-                if (lane >= d) incl += t;
-            }
-            ws.prefix[lane] = incl - c;
-            __syncwarp();
-        }
-    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int r0 = u * kWarpSliceUnits + lane * kUnitsPerVec;
         const long long p0 = cfirst + r0;
-        const unsigned long long w2 =
-            (unsigned long long)bits[r0 >> 5] | ((unsigned long long)bits[(r0 >> 5) + 1] << 32);
-        const uint32_t s9 = (uint32_t)(w2 >> (r0 & 31)) & 0x1FFu;  // string starts at units r0 .. r0+8
-        uint32_t st_lo, st_hi;
-        bits_to_flags(s9 & 0xFFu, st_lo, st_hi);
+        const uint2 st = *reinterpret_cast<const uint2 *>(ws.starts + r0);  // starts at units r0 .. r0+7
+        const uint32_t st_next = ws.starts[r0 + 8] >> 7;                   // a start at unit r0+8
         uint32_t bad_lo, bad_hi;
-        vec_bad<U>(cb, u, from_prev, from_next, st_lo, st_hi, (s9 >> 8) & 1u, bad_lo, bad_hi);
+        vec_bad<U>(cb, u, from_prev, from_next, st.x, st.y, st_next, bad_lo, bad_hi);
         if (edge) {
             uint32_t vlo, vhi;
             bits_to_flags(batch_valid_bits8(p0, lo, hi), vlo, vhi);
@@ -243,11 +230,18 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
                 const long long p = p0 + b;
                 long long a_i, start;
                 if (simple) {
-                    // starts at or before p inside the chunk, all distinct
-                    const int r = r0 + b;
-                    const int k = (int)ws.prefix[r >> 5] + __popc(bits[r >> 5] & (0xFFFFFFFFu >> (31 - (r & 31))));
-                    a_i = s_first - 1 + k;
-                    start = ws.window[k];
+                    // largest window index whose offset is <= p (empty strings
+                    // share offsets; the last of them is the one holding p)
+                    int wa = -1, wb = 31;
+                    while (wa < wb) {
+                        const int mid = (wa + wb + 1) >> 1;
+                        if (ws.win[mid] <= p)
+                            wa = mid;
+                        else
+                            wb = mid - 1;
+                    }
+                    a_i = base_first + wa;
+                    start = wa >= 0 ? ws.win[wa] : ws.win_prev;
                 } else {
                     a_i = s_lo;
                     long long b_i = s_last > s_lo ? s_last : s_lo;
@@ -277,7 +271,7 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
     __shared__ WarpScratch<U> s_scratch[kBlockThreads / 32];
 
     const int lane = threadIdx.x & 31;
-    WarpScratch<U> &bits = s_scratch[threadIdx.x >> 5];
+    WarpScratch<U> &ws = s_scratch[threadIdx.x >> 5];
 
     const long long lo = A.offsets[0];
     const long long hi = A.offsets[A.count];
@@ -299,14 +293,14 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
             const BatchChunk<U> v = nv;
             if (c + 1 < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + (c + 1) * (32LL * U), lo, hi, lane, nv);
             const long long cfirst = (vbeg + c * (32LL * U)) * 8 - A.a;
-            process_batch_chunk<MODE, ST, U>(A, cfirst, lo, hi, v, lane, bits, hint);
+            process_batch_chunk<MODE, ST, U>(A, cfirst, lo, hi, v, lane, ws, hint);
         }
     } else {
         for (long long c = c_begin; c < c_end; ++c) {
             const long long vfirst = vbeg + c * (32LL * U);
             BatchChunk<U> v;
             load_batch_chunk<MODE, U>(A, vin, vfirst, lo, hi, lane, v);
-            process_batch_chunk<MODE, ST, U>(A, vfirst * 8 - A.a, lo, hi, v, lane, bits, hint);
+            process_batch_chunk<MODE, ST, U>(A, vfirst * 8 - A.a, lo, hi, v, lane, ws, hint);
         }
     }
 }
