@@ -252,7 +252,10 @@ int utf16_selftest_bounded_wait(int64_t limit_ns);
  * the next.  Small requests (< small_request_bytes) are packed through a
  * pinned staging buffer per slot; larger ones are copied straight from and to
  * the caller's buffers (pinned buffers overlap; pageable ones are copied
- * synchronously by the CUDA runtime).  Each string of a batch is repaired on
+ * synchronously by the CUDA runtime).  With direct_host_access, small
+ * requests in pinned buffers are read and written by the GPU directly (one
+ * gather and one scatter kernel per batch), which keeps the CPU out of the
+ * data path.  Each string of a batch is repaired on
  * its own, so a request's result is the same alone and in any mix.
  * ===================================================================== */
 typedef struct utf16_server utf16_server;
@@ -267,6 +270,9 @@ typedef struct {
     int64_t inject_fail_mod;      /* testing: 0 = off; k > 0 = the admission of every request whose
                                      ticket % k == k - 1 fails with UTF16_ENOMEM (host-side fault
                                      injection; other requests are unaffected) */
+    int direct_host_access;       /* 1: a small request whose host buffers are pinned (page-locked, mapped) is
+                                     copied in and out by the GPU itself, in 8 KiB pieces (no CPU copies; each
+                                     submit then queries the buffers' attributes); 0 (default): staged */
 } utf16_server_options;
 
 typedef struct {

@@ -107,8 +107,67 @@ struct Request {
     int64_t first_bad = -1;
     int status = UTF16_OK;
     bool large = false;
+    bool direct = false;          // small request whose buffers the GPU reads / writes itself (pinned host memory)
+    const uint16_t *dev_in = nullptr;   // device view of `in` (direct requests)
+    uint16_t *dev_out = nullptr;        // device view of `out` (direct requests)
     int64_t dev_off = 0;  // unit offset inside the batch
 };
+
+// One direct request for the gather / scatter kernels.
+struct CopyDesc {
+    const uint16_t *src;  // caller's input (device view of pinned host memory)
+    uint16_t *dst;        // caller's output (same)
+    long long off;        // unit offset in the batch
+    long long n;
+};
+
+constexpr long long kPieceUnits = 4096;  // direct requests are copied in pieces of at most 8 KiB
+
+// Copy pieces of requests between the callers' pinned host buffers and the
+// batch in device memory: one warp per piece, four 16-byte loads in flight
+// per lane before the stores (the host side is a long-latency link), unit
+// copies when the host side is not 16-byte aligned (the batch side always is).
+template <bool GATHER>
+__global__ void __launch_bounds__(256) copy_requests_kernel(const CopyDesc *descs, int count, uint16_t *units) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int i = gwarp; i < count; i += nwarps) {
+        const CopyDesc c = descs[i];
+        uint16_t *dev = units + c.off;
+        const uint16_t *src = GATHER ? c.src : dev;
+        uint16_t *dst = GATHER ? dev : c.dst;
+        const bool vec = ((((uintptr_t)c.src | (uintptr_t)c.dst) & 15u) == 0);
+        const int n = (int)c.n;
+        const int vecs = vec ? n / 8 : 0;
+        for (int base = 0; base < vecs; base += 128) {
+            uint4 buf[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = base + k * 32 + lane;
+                if (j < vecs) buf[k] = reinterpret_cast<const uint4 *>(src)[j];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = base + k * 32 + lane;
+                if (j < vecs) reinterpret_cast<uint4 *>(dst)[j] = buf[k];
+            }
+        }
+        for (int base = vecs * 8; base < n; base += 256) {
+            uint16_t buf[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int j = base + k * 32 + lane;
+                if (j < n) buf[k] = src[j];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int j = base + k * 32 + lane;
+                if (j < n) dst[j] = buf[k];
+            }
+        }
+    }
+}
 
 struct BatchSlot {
     std::vector<Request> reqs;
@@ -116,13 +175,16 @@ struct BatchSlot {
     uint16_t *d_units = nullptr;
     long long *d_offsets = nullptr;
     long long *d_first = nullptr;
-    char *h_stage = nullptr;  // pinned: [offsets][first][small units]
+    CopyDesc *d_desc = nullptr;
+    char *h_stage = nullptr;  // pinned: [offsets][first][descriptors][staged small units]
     int64_t h_cap = 0;
     int64_t small_units = 0;
     int64_t total_units = 0;
     int64_t head_bytes = 0;  // offsets + first-error region, 256-aligned (same on device and host)
     int64_t first_off = 0;   // byte offset of the first-error array in that region
     int64_t strings = 0;     // strings of the launched batch (requests plus padding strings)
+    int64_t desc_off = 0;    // byte offset of the direct-request descriptors in the head region
+    int ndirect = 0;
     std::vector<int> req_of_string;  // request index of each string, -1 for padding
     cudaEvent_t ev_h2d = nullptr, ev_kernel = nullptr, ev_done = nullptr;
     int status = UTF16_OK;
@@ -131,10 +193,15 @@ struct BatchSlot {
 // Head layout of a batch of up to `reqs` requests (at most 2*reqs strings:
 // a padding string may precede each aligned large request): offsets, then
 // first-error indices, each 256-byte aligned.
-static void batch_head_layout(int64_t reqs, int64_t &first_off, int64_t &head_bytes) {
+static void batch_head_layout(int64_t reqs, int64_t pieces, int64_t &first_off, int64_t &head_bytes,
+                              int64_t *desc_off = nullptr) {
     first_off = align_up((2 * reqs + 2) * 8, 256);
-    head_bytes = first_off + align_up(2 * reqs * 8, 256);
+    const int64_t d = first_off + align_up(2 * reqs * 8, 256);
+    if (desc_off) *desc_off = d;
+    head_bytes = d + align_up(pieces * (int64_t)sizeof(CopyDesc), 256);
 }
+
+static int64_t pieces_of(const Request &r) { return r.direct ? (r.n + kPieceUnits - 1) / kPieceUnits : 0; }
 
 }  // namespace u16wf
 
@@ -172,41 +239,53 @@ static void complete_request(utf16_server *S, Request &r, int status) {
 }
 
 // Build and launch one batch on slot `si` from the admitted requests in it.
-// Small requests are packed first (staged through pinned memory), then the
-// large ones, each at a 16-byte aligned unit offset so that its own copies
-// are aligned; a gap before a large request is a padding string of its own,
-// so every request is exactly one string of the ragged batch.
+// Staged small requests are packed first (through the slot's pinned staging
+// buffer); then direct small requests (gathered and scattered by the GPU
+// from and to the callers' pinned buffers) and large ones (copy engines),
+// each at a 16-byte aligned unit offset.  A gap before an aligned request is
+// a padding string of its own, so every request is exactly one string.
 static void launch_batch_slot(utf16_server *S, int si) {
     BatchSlot &b = S->slots[(size_t)si];
-    std::stable_partition(b.reqs.begin(), b.reqs.end(), [](const Request &r) { return !r.large; });
+    std::stable_partition(b.reqs.begin(), b.reqs.end(), [](const Request &r) { return !r.large && !r.direct; });
     int64_t *h_off = (int64_t *)b.h_stage;
     int64_t *h_first = (int64_t *)(b.h_stage + b.first_off);
+    CopyDesc *h_desc = (CopyDesc *)(b.h_stage + b.desc_off);
     uint16_t *h_units = (uint16_t *)(b.h_stage + b.head_bytes);
     int64_t pos = 0;
     int64_t strings = 0;
+    int nd = 0;
     b.req_of_string.clear();
+    b.small_units = 0;
     h_off[0] = 0;
     for (int i = 0; i < (int)b.reqs.size(); ++i) {
         Request &r = b.reqs[(size_t)i];
-        if (!r.large) {
+        const bool staged = !r.large && !r.direct;
+        if (staged) {
             memcpy(h_units + pos, r.in, (size_t)r.n * 2u);
         } else if (pos % 8 != 0) {
             pos = align_up(pos, 8);
             h_off[++strings] = pos;  // padding string
             b.req_of_string.push_back(-1);
         }
-        if (!r.large) b.small_units = pos + r.n;
+        if (r.direct)
+            for (int64_t j = 0; j < r.n; j += kPieceUnits)
+                h_desc[nd++] = CopyDesc{r.dev_in + j, r.dev_out + j, (long long)(pos + j),
+                                        (long long)std::min<int64_t>(kPieceUnits, r.n - j)};
         r.dev_off = pos;
         pos += r.n;
+        if (staged) b.small_units = pos;
         h_off[++strings] = pos;
         b.req_of_string.push_back(i);
     }
     b.total_units = pos;
     b.strings = strings;
+    b.ndirect = nd;
     b.status = UTF16_OK;
 
     cudaError_t e = cudaMemcpyAsync(b.d_offsets, h_off, (size_t)(strings + 1) * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, S->s_h2d);
+    if (e == cudaSuccess && nd)
+        e = cudaMemcpyAsync(b.d_desc, h_desc, (size_t)nd * sizeof(CopyDesc), cudaMemcpyHostToDevice, S->s_h2d);
     if (e == cudaSuccess && b.small_units)
         e = cudaMemcpyAsync(b.d_units, h_units, (size_t)b.small_units * 2u, cudaMemcpyHostToDevice, S->s_h2d);
     for (const Request &r : b.reqs)
@@ -214,6 +293,11 @@ static void launch_batch_slot(utf16_server *S, int si) {
             e = cudaMemcpyAsync(b.d_units + r.dev_off, r.in, (size_t)r.n * 2u, cudaMemcpyHostToDevice, S->s_h2d);
     if (e == cudaSuccess) e = cudaEventRecord(b.ev_h2d, S->s_h2d);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_comp, b.ev_h2d, 0);
+    const int copy_blocks = std::max(1, std::min(S->ctx->sms * 8, (nd + 7) / 8));
+    if (e == cudaSuccess && nd) {
+        copy_requests_kernel<true><<<copy_blocks, 256, 0, S->s_comp>>>(b.d_desc, nd, b.d_units);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         BatchLaunch L;
         L.in = b.d_units;
@@ -224,6 +308,10 @@ static void launch_batch_slot(utf16_server *S, int si) {
         L.mode = kModeInPlaceFirst;
         configure_batch(S->ctx, S->ctx->batch_config(b.total_units, strings), L);
         e = launch_batch(L, S->s_comp);
+    }
+    if (e == cudaSuccess && nd) {
+        copy_requests_kernel<false><<<copy_blocks, 256, 0, S->s_comp>>>(b.d_desc, nd, b.d_units);
+        e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(b.ev_kernel, S->s_comp);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_d2h, b.ev_kernel, 0);
@@ -253,8 +341,8 @@ static void scheduler_main(utf16_server *S) {
         b.reqs.clear();
         // Admission in arrival order: stop at the first request that does not
         // fit (keeps FIFO order; a later, smaller request does not overtake).
-        int64_t nreq = 0, small_units = 0, units = 0, bytes = 0, need = 0;
-        int64_t first_off = 0, head = 0;
+        int64_t nreq = 0, pieces = 0, small_units = 0, units = 0, bytes = 0, need = 0;
+        int64_t first_off = 0, head = 0, desc_off = 0;
         while (!S->pending.empty()) {
             Request &r = S->pending.front();
             if (o.inject_fail_mod > 0 && (int64_t)(r.ticket % (uint64_t)o.inject_fail_mod) == o.inject_fail_mod - 1) {
@@ -267,21 +355,25 @@ static void scheduler_main(utf16_server *S) {
                 continue;
             }
             const bool large = r.n * 2 >= o.small_request_bytes;
-            const int64_t u2 = (large ? align_up(units, 8) : units) + r.n;
-            const int64_t sm2 = small_units + (large ? 0 : r.n);
-            int64_t f2, h2;
-            batch_head_layout(nreq + 1, f2, h2);
+            const bool aligned = large || r.direct;
+            const int64_t u2 = (aligned ? align_up(units, 8) : units) + r.n;
+            const int64_t sm2 = small_units + (aligned ? 0 : r.n);
+            int64_t f2, h2, d2;
+            r.large = large;
+            batch_head_layout(nreq + 1, pieces + pieces_of(r), f2, h2, &d2);
             const int64_t need2 = h2 + align_up(u2 * 2, 256);
             if (2 * (nreq + 1) > o.max_batch_strings || bytes + r.n * 2 > o.max_batch_bytes ||
                 h2 + sm2 * 2 > b.h_cap || need2 > S->ring->cap())
                 break;
             nreq += 1;
+            pieces += pieces_of(r);
             units = u2;
             small_units = sm2;
             bytes += r.n * 2;
             need = need2;
             first_off = f2;
             head = h2;
+            desc_off = d2;
             r.large = large;
             b.reqs.push_back(r);
             S->pending.pop_front();
@@ -304,10 +396,12 @@ static void scheduler_main(utf16_server *S) {
         b.ring_off = ring_off;
         b.first_off = first_off;
         b.head_bytes = head;
+        b.desc_off = desc_off;
         b.small_units = 0;
         char *base = S->arena + ring_off;
         b.d_offsets = (long long *)base;
         b.d_first = (long long *)(base + first_off);
+        b.d_desc = (CopyDesc *)(base + desc_off);
         b.d_units = (uint16_t *)(base + head);
         S->stats.batches++;
         S->stats.max_batch_requests = std::max(S->stats.max_batch_requests, nreq);
@@ -346,7 +440,7 @@ static void completer_main(utf16_server *S) {
             const int ri = b.req_of_string[(size_t)s];
             if (ri < 0) continue;
             Request &r = b.reqs[(size_t)ri];
-            if (status == UTF16_OK && !r.large) memcpy(r.out, h_units + r.dev_off, (size_t)r.n * 2u);
+            if (status == UTF16_OK && !r.large && !r.direct) memcpy(r.out, h_units + r.dev_off, (size_t)r.n * 2u);
             r.first_bad = h_first[s];
         }
         const int64_t t_done = now_ns();
@@ -383,6 +477,7 @@ int utf16_server_default_options(utf16_server_options *o) {
     o->staging_bytes = 64LL << 20;
     o->small_request_bytes = 256LL << 10;
     o->inject_fail_mod = 0;
+    o->direct_host_access = 0;
     return UTF16_OK;
 }
 
@@ -391,7 +486,7 @@ int utf16_server_create(const utf16_server_options *opt, utf16_server **out) {
     const utf16_server_options &o = *opt;
     if (o.hbm_budget_bytes < (1 << 20) || o.max_batch_strings < 2 || o.max_batch_bytes < 1024 ||
         o.max_inflight_batches < 1 || o.max_inflight_batches > 64 || o.staging_bytes < 4096 ||
-        o.small_request_bytes < 0 || o.inject_fail_mod < 0)
+        o.small_request_bytes < 0 || o.inject_fail_mod < 0 || o.direct_host_access < 0 || o.direct_host_access > 1)
         return UTF16_EINVAL;
     std::unique_ptr<utf16_server> S(new utf16_server());
     S->opt = o;
@@ -440,6 +535,23 @@ int utf16_server_submit(utf16_server *S, const uint16_t *host_in, uint16_t *host
     if (need > S->opt.hbm_budget_bytes || n * 2 > S->opt.max_batch_bytes ||
         (!large && n * 2 + 1024 > S->opt.staging_bytes))
         return UTF16_ENOMEM;
+    // Small requests whose buffers are pinned host memory are gathered and
+    // scattered by the GPU itself (no staging copies on the CPU).
+    bool direct = false;
+    const uint16_t *dev_in = nullptr;
+    uint16_t *dev_out = nullptr;
+    if (S->opt.direct_host_access && n > 0 && !large) {
+        cudaPointerAttributes ai, ao;
+        if (cudaPointerGetAttributes(&ai, host_in) == cudaSuccess && ai.type == cudaMemoryTypeHost &&
+            ai.devicePointer && cudaPointerGetAttributes(&ao, host_out) == cudaSuccess &&
+            ao.type == cudaMemoryTypeHost && ao.devicePointer) {
+            direct = true;
+            dev_in = (const uint16_t *)ai.devicePointer;
+            dev_out = (uint16_t *)ao.devicePointer;
+        } else {
+            cudaGetLastError();
+        }
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stopping) return UTF16_ECLOSED;
     Request r;
@@ -447,6 +559,9 @@ int utf16_server_submit(utf16_server *S, const uint16_t *host_in, uint16_t *host
     r.in = host_in;
     r.out = host_out;
     r.n = n;
+    r.direct = direct;
+    r.dev_in = dev_in;
+    r.dev_out = dev_out;
     r.arrival_ns = arrival_ns > 0 ? arrival_ns : now_ns();
     if (n == 0) {
         r.first_bad = 0;

@@ -83,16 +83,42 @@ def test_same_alone_and_in_the_mix(pkg):
     assert np.all(lat > 0)
 
 
-def test_pinned_host_buffers(pkg):
+@pytest.mark.parametrize("direct", [1, 0])
+def test_pinned_host_buffers(pkg, direct):
+    """Pinned buffers: small requests gathered / scattered by the GPU itself
+    (direct) or staged through pinned staging; large ones by copy engines."""
     import torch
-    reqs = _requests(120, 13)
+    reqs = _requests(300, 13)
     want = _expect(reqs)
     ins = [torch.from_numpy(u.view(np.int16)).pin_memory() for u in reqs]
-    outs = [torch.empty_like(t).pin_memory() for t in ins]
-    with pkg.Server(small_request_bytes=32 << 10) as srv:
+    outs = [torch.full_like(t, 0x5A5A).pin_memory() for t in ins]
+    with pkg.Server(small_request_bytes=32 << 10, direct_host_access=direct) as srv:
         lat, fb = srv.replay(ins, outs, rate_per_s=0, seed=4)
+        lat2, fb2 = srv.replay(ins, outs, rate_per_s=20_000, seed=5)
     for i, (w, f) in enumerate(want):
-        assert np.array_equal(outs[i].numpy().view(np.uint16), w) and fb[i] == f, i
+        assert np.array_equal(outs[i].numpy().view(np.uint16), w) and fb[i] == f and fb2[i] == f, i
+
+
+def test_pinned_and_pageable_in_one_batch(pkg):
+    import torch
+    reqs = _requests(300, 17, big=False)
+    want = _expect(reqs)
+    ins, outs = [], []
+    for i, u in enumerate(reqs):
+        if i % 3 == 0:  # pageable numpy buffers: staged
+            ins.append(u.copy())
+            outs.append(np.zeros_like(u))
+        else:           # pinned: gathered / scattered by the GPU; odd offsets exercise unaligned copies
+            t = torch.from_numpy(np.concatenate([np.zeros(i % 8, np.uint16), u]).view(np.int16)).pin_memory()
+            ins.append(t[i % 8:])
+            outs.append(torch.zeros(u.size + 8, dtype=torch.int16).pin_memory()[(i * 5) % 8:][:u.size])
+    with pkg.Server(max_inflight_batches=2, direct_host_access=1) as srv:
+        lat, fb = srv.replay(ins, outs, rate_per_s=0, seed=6)
+        st = srv.stats()
+    assert st["max_batch_requests"] > 10
+    for i, (w, f) in enumerate(want):
+        got = outs[i] if isinstance(outs[i], np.ndarray) else outs[i].numpy().view(np.uint16)
+        assert np.array_equal(got, w) and fb[i] == f, i
 
 
 def test_injected_admission_failures_leave_others_exact(pkg):
