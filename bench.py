@@ -141,14 +141,15 @@ def kernel_source_hash(files=KERNEL_SOURCES):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(name):
-    """DRAM bytes per launch from the committed ncu record, if it was taken
-    on the current kernel sources (else None)."""
+def recorded_traffic(name, variant, units_per_thread):
+    """DRAM bytes per launch from the committed ncu record for this kernel and
+    launch configuration, if it was taken on the current kernel sources (else
+    None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d[name]
+        e = d[name]["configs"][f"variant{variant}_u{units_per_thread}"]
         if e.get("kernel_hash") != kernel_source_hash(e.get("sources", KERNEL_SOURCES)):
             return None
         return float(e["dram_bytes_per_launch"])
@@ -238,6 +239,17 @@ def capture_graph(torch, fn):
         fn()
     torch.cuda.synchronize()
     return g
+
+
+def graph_calls_ms(torch, fn, stream, calls=64, replays=8, fn_makes_all=False):
+    """GPU time (ms) per call of a CUDA graph that holds `calls` consecutive
+    calls, replayed `replays` times: back-to-back calls without the host's
+    launch overhead.  fn() makes one call, or all `calls` of them when
+    fn_makes_all is set."""
+    g = capture_graph(torch, fn if fn_makes_all else (lambda: [fn() for _ in range(calls)]))
+    g.replay()
+    torch.cuda.synchronize()
+    return time_launches(torch, g.replay, replays, stream) / (replays * calls)
 
 
 def time_launches(torch, fn, steps, stream):
@@ -345,6 +357,9 @@ def main():
     d_out = torch.empty_like(d_in)
     fb = torch.empty(1, dtype=torch.int64, device="cuda")
 
+    tuned = wf.autotune_single(d_in, d_out, reps=5)  # launch configuration for this size, as a user would
+    torch.cuda.synchronize()
+
     def step():
         wf.to_well_formed_first_bad(d_in, d_out, fb, stream=stream)
 
@@ -372,12 +387,13 @@ def main():
 
     peak, peak_kind = measured_peaks()
     per_rank_hbm = n * 4 / (ms_per_step * 1e-3) / 1e9
-    traffic = recorded_traffic("single_out_fb_1GiB")
+    traffic = recorded_traffic("single_out_fb_1GiB", tuned.single_variant, tuned.single_units_per_thread)
     roofline = {"bound": "hbm", "achieved": round(per_rank_hbm, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(per_rank_hbm / peak, 4), "peak_kind": peak_kind,
                 "frac_of_nominal_8tbs": round(per_rank_hbm / NOMINAL_HBM_GBS, 4),
                 "traffic": traffic, "algorithmic_bytes_per_launch": n * 4,
-                "kernel": "single_kernel<out-of-place, first-error, 16-byte stores, U=4>"}
+                "kernel": f"fused out-of-place + first-error kernel, variant {tuned.single_variant}, "
+                          f"U={tuned.single_units_per_thread}, blocks/SM={tuned.single_blocks_per_sm or 'max'}"}
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -386,6 +402,7 @@ def main():
         "config": {"workload": WORKLOAD, "units": n, "l2": "inputs larger than L2 (1 GiB per step), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
+        "launch_config": {"autotuned": tuned.as_dict(), "block_threads": 256, "vector_bytes": 16},
         "gpu_launches": args.steps,
         "clocks": clk,
     }
@@ -436,7 +453,8 @@ def variants(torch, wf, stream, d_in, d_out, u_main):
 
     def rec(name, n, ms, bytes_per_unit):
         res[name] = {"input_gbs": round(n * 2 / (ms * 1e-3) / 1e9, 1),
-                     "hbm_frac": round(n * bytes_per_unit / (ms * 1e-3) / 1e9 / peak, 4), "ms": round(ms, 4)}
+                     "hbm_frac": round(n * bytes_per_unit / (ms * 1e-3) / 1e9 / peak, 4), "ms": round(ms, 4),
+                     "us": round(ms * 1e3, 2)}
 
     steps = 5
     n = u_main.size
@@ -498,6 +516,21 @@ def variants(torch, wf, stream, d_in, d_out, u_main):
     g = capture_graph(torch, lambda: wf.to_well_formed_first_bad(small, s_out, s_fb))
     ms = time_launches(torch, g.replay, 200, stream) / 200
     rec("1MiB_mixed_out_first_bad_L2_resident_graph_replay", small.numel(), ms, 4)
+    ms = graph_calls_ms(torch, lambda: wf.to_well_formed_first_bad(small, s_out, s_fb), stream)
+    rec("1MiB_mixed_out_first_bad_L2_resident_back_to_back", small.numel(), ms, 4)
+    res["1MiB_mixed_out_first_bad_L2_resident_back_to_back"]["note"] = (
+        "64 calls captured in one CUDA graph: GPU time per call without host launch overhead")
+    # the same calls over 256 different 1 MiB strings (1 GiB in + out > L2): every call reads HBM
+    ring = 256
+    rot_in = d_in[: ring * small.numel()].view(ring, -1)
+    rot_out = d_out[: ring * small.numel()].view(ring, -1)
+    rot_in.copy_(small.expand(ring, -1))
+    rot_fb = torch.empty(ring, dtype=torch.int64, device="cuda")
+    ms = graph_calls_ms(torch, lambda: [wf.to_well_formed_first_bad(rot_in[i], rot_out[i], rot_fb[i:i + 1])
+                                        for i in range(ring)], stream, calls=ring, fn_makes_all=True)
+    rec("1MiB_mixed_out_first_bad_256_buffer_rotation", small.numel(), ms, 4)
+    res["1MiB_mixed_out_first_bad_256_buffer_rotation"]["note"] = (
+        "256 calls on 256 distinct 1 MiB strings (1 GiB in + 1 GiB out, larger than L2) in one CUDA graph")
     d_in.copy_(pristine)
     del pristine
     return res
@@ -567,19 +600,37 @@ def paper_measure(torch, wf, stream):
         for k in range(1, 129):
             n = full * k // 128
             a, b = d_in[:n], d_out[:n]
-            g = capture_graph(torch, lambda: wf.to_well_formed_first_bad(a, b, fb))
-            ms = time_launches(torch, g.replay, 50, stream) / 50
+            ms = graph_calls_ms(torch, lambda: wf.to_well_formed_first_bad(a, b, fb), stream, calls=32, replays=4)
             curve.append([n, round(n * 2 / (ms * 1e-3) / 1e9, 2)])
+        g = capture_graph(torch, lambda: wf.to_well_formed_first_bad(d_in, d_out, fb))
+        lat = time_launches(torch, g.replay, 200, stream) / 200
         res[f"1M_units_{label}"] = {"input_gbs": curve[-1][1], "us_per_call": round(full * 2 / curve[-1][1] / 1e3, 2),
+                                    "us_per_graph_replay_from_host": round(lat * 1e3, 2),
                                     "size_sweep_units_vs_gbs": curve}
     u = workloads.paper_mix(1024, 0.0, 0.10, seed=workloads.SEED_BASE + 6)
     d_in = torch.from_numpy(u.view(np.int16)).cuda()
     d_out = torch.empty_like(d_in)
     fb = torch.empty(1, dtype=torch.int64, device="cuda")
     g = capture_graph(torch, lambda: wf.to_well_formed_first_bad(d_in, d_out, fb))
-    ms = time_launches(torch, g.replay, 200, stream) / 200
+    lat = time_launches(torch, g.replay, 200, stream) / 200
+    ms = graph_calls_ms(torch, lambda: wf.to_well_formed_first_bad(d_in, d_out, fb), stream)
     res["1024_units_5pct_low_5pct_high"] = {"us_per_call": round(ms * 1e3, 2),
-                                           "input_gib_s": round(2048 / (ms * 1e-3) / 2 ** 30, 3)}
+                                           "input_gib_s": round(2048 / (ms * 1e-3) / 2 ** 30, 3),
+                                           "us_per_graph_replay_from_host": round(lat * 1e3, 2)}
+    # the form meant for short strings: many of them in one ragged batch
+    count = 4096
+    offs = np.arange(count + 1, dtype=np.int64) * 1024
+    many = np.tile(u, count)
+    d_many = torch.from_numpy(many.view(np.int16)).cuda()
+    d_offs = torch.from_numpy(offs).cuda()
+    d_many_out = torch.empty_like(d_many)
+    fbb = torch.empty(count, dtype=torch.int64, device="cuda")
+    ms = graph_calls_ms(torch, lambda: (wf.to_well_formed_batch(d_many, d_offs, d_many_out),
+                                        wf.first_error_index_batch(d_many, d_offs, fbb)), stream, calls=8, replays=8)
+    res["1024_units_x4096_ragged_batch"] = {"strings": count, "us_per_batch": round(ms * 1e3, 2),
+                                           "input_gib_s": round(count * 2048 / (ms * 1e-3) / 2 ** 30, 1),
+                                           "note": "repair and per-string first-error index of 4096 such strings, "
+                                                   "two launches, CUDA graph"}
     res["paper_context"] = ("Apple M4 simdutf arm64: 18.9 / 16.3 GB/s (0 % / 0.1 %), Xeon Gold 6338 haswell: "
                             "7.8 / 7.6 GB/s, 1,000,000 units (Tables 4-5); Node.js 25 1024-char string: 16 / 11 GiB/s "
                             "(Table 6). CPU figures, context only.")

@@ -222,6 +222,15 @@ int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int64_t *offse
                          utf16_config *best);
 
 /*
+ * Tuned entries (what the autotuner stored), for saving and restoring a
+ * tuning cache.  op: 0 = single strings (bucket = floor(log2(n))), 1 =
+ * batches (bucket = floor(log2(num_strings))); bucket 0..63.
+ * utf16_get_tuned returns UTF16_EAGAIN when nothing is tuned for the bucket.
+ */
+int utf16_get_tuned(int op, int bucket, utf16_config *cfg);
+int utf16_set_tuned(int op, int bucket, const utf16_config *cfg);
+
+/*
  * UTF16_ETIMEOUT if a kernel of this device gave up a bounded wait (a TMA
  * copy that did not complete within one second) since the last call, which
  * means its outputs are not valid; UTF16_OK otherwise.  Synchronises the

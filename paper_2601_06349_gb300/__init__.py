@@ -84,6 +84,8 @@ def _declare(lib):
         "utf16_autotune_single": ([vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_autotune_batch": ([vp, vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_check_device_errors": ([], ctypes.c_int),
+        "utf16_get_tuned": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
+        "utf16_set_tuned": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_error_positions": ([vp, i64, vp, i64, vp, vp], ctypes.c_int),
         "utf16_selftest_bounded_wait": ([i64], ctypes.c_int),
         "utf16_to_well_formed_first_bad_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
@@ -513,3 +515,46 @@ class Arena:
         if getattr(self, "_h", None):
             lib().utf16_arena_destroy(self._h)
             self._h = None
+
+
+def save_tuning(path: str) -> dict:
+    """Write the current device's tuned entries to a JSON file keyed by GPU
+    name; returns what was written."""
+    import json
+    torch = _torch()
+    name = torch.cuda.get_device_name()
+    entries = {}
+    for op, key in ((0, "single"), (1, "batch")):
+        for bucket in range(64):
+            c = Config()
+            if lib().utf16_get_tuned(op, bucket, ctypes.byref(c)) == OK:
+                entries.setdefault(key, {})[str(bucket)] = c.as_dict()
+    data = {}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    data[name] = entries
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    return entries
+
+
+def load_tuning(path: str) -> int:
+    """Restore tuned entries saved for this GPU name; returns how many."""
+    import json
+    torch = _torch()
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return 0
+    entries = data.get(torch.cuda.get_device_name(), {})
+    count = 0
+    for op, key in ((0, "single"), (1, "batch")):
+        for bucket, fields in entries.get(key, {}).items():
+            c = Config(**{k: int(v) for k, v in fields.items() if k in dict(Config._fields_)})
+            _check(lib().utf16_set_tuned(op, int(bucket), ctypes.byref(c)), "utf16_set_tuned")
+            count += 1
+    return count

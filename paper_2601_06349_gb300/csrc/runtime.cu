@@ -329,6 +329,34 @@ int utf16_set_config(const utf16_config *cfg) {
     return UTF16_OK;
 }
 
+int utf16_get_tuned(int op, int bucket, utf16_config *cfg) {
+    if ((op != 0 && op != 1) || bucket < 0 || bucket >= kBuckets || !cfg) return UTF16_EINVAL;
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const bool has = op == 0 ? ctx->single_has[bucket] : ctx->batch_has[bucket];
+    if (!has) return UTF16_EAGAIN;
+    *cfg = op == 0 ? ctx->single_tuned[bucket] : ctx->batch_tuned[bucket];
+    return UTF16_OK;
+}
+
+int utf16_set_tuned(int op, int bucket, const utf16_config *cfg) {
+    if ((op != 0 && op != 1) || bucket < 0 || bucket >= kBuckets || !cfg || !config_valid(*cfg)) return UTF16_EINVAL;
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (op == 0) {
+        ctx->single_tuned[bucket] = *cfg;
+        ctx->single_has[bucket] = true;
+    } else {
+        ctx->batch_tuned[bucket] = *cfg;
+        ctx->batch_has[bucket] = true;
+    }
+    return UTF16_OK;
+}
+
 int utf16_selftest_bounded_wait(int64_t limit_ns) {
     if (limit_ns <= 0 || limit_ns > 2000000000LL) return UTF16_EINVAL;
     DeviceCtx *ctx;

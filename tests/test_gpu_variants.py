@@ -122,3 +122,19 @@ def test_bounded_wait_gives_up_and_reports(pkg):
     u = workloads.mixed(100_000, 1e-2, seed=5)
     d = to_dev(u)
     assert pkg.first_error_index_sync(d) == oracle.first_bad(u)
+
+
+def test_tuning_cache_round_trip(pkg, tmp_path):
+    import torch
+    u = workloads.mixed(4 << 20, 1e-2, seed=53)
+    d = to_dev(u)
+    cfg = pkg.autotune_single(d, torch.empty_like(d), reps=2)
+    path = str(tmp_path / "tuning.json")
+    saved = pkg.save_tuning(path)
+    assert "single" in saved and str((u.size).bit_length() - 1) in saved["single"]
+    pkg.set_config(pkg.get_config())  # clears tuned entries
+    assert pkg.lib().utf16_get_tuned(0, u.size.bit_length() - 1, pkg.Config()) == pkg.EAGAIN
+    assert pkg.load_tuning(path) >= 1
+    c = pkg.Config()
+    assert pkg.lib().utf16_get_tuned(0, u.size.bit_length() - 1, c) == 0
+    assert c.as_dict() == cfg.as_dict()
