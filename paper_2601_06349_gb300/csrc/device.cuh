@@ -142,9 +142,11 @@ __device__ __forceinline__ uint32_t chunk_surrogates(const uint4 (&v)[U], ChunkB
 // slice (lane 0's in the next slice), or the halo unit just outside the chunk:
 //   halo_prev   lane 0: the unit before the chunk is a high surrogate
 //   halo_next   lane 31: the unit after the chunk is a low surrogate
+// chunk_classes_prev() does the first half (classes and from_prev),
+// chunk_next_low() the second.
 template <int U>
-__device__ __forceinline__ void chunk_classes(ChunkBits<U> &cb, uint32_t halo_prev, uint32_t halo_next, int lane,
-                                              uint32_t &from_prev, uint32_t &from_next) {
+__device__ __forceinline__ void chunk_classes_prev(ChunkBits<U> &cb, uint32_t halo_prev, int lane,
+                                                   uint32_t &from_prev) {
 #pragma unroll
     for (int i = 0; i < 2 * U; ++i) {
         const uint32_t lowhalf = low_half_flags(cb.a[i]);
@@ -152,25 +154,62 @@ __device__ __forceinline__ void chunk_classes(ChunkBits<U> &cb, uint32_t halo_pr
         cb.a[i] = sur & ~lowhalf;
         cb.b[i] = sur & lowhalf;
     }
-    // Byte u of last_h: byte 3 of h_hi[u] (flag of unit 7 of vector u at its
-    // bit 7); byte u of first_l: byte 0 of l_lo[u] (flag of unit 0).
-    uint32_t last_h, first_l;
+    // Byte u of last_h: byte 3 of h_hi[u] (flag of unit 7 of vector u at its bit 7).
+    uint32_t last_h;
     if constexpr (U == 4) {
         last_h = prmt(prmt(cb.a[1], cb.a[3], 0x0073), prmt(cb.a[5], cb.a[7], 0x0073), 0x5410);
-        first_l = prmt(prmt(cb.b[0], cb.b[2], 0x0040), prmt(cb.b[4], cb.b[6], 0x0040), 0x5410);
     } else if constexpr (U == 2) {
         last_h = prmt(cb.a[1], cb.a[3], 0x0073) & 0xFFFFu;  // bytes 2, 3 are copies, not flags
-        first_l = prmt(cb.b[0], cb.b[2], 0x0040) & 0xFFFFu;
     } else {
         last_h = cb.a[2 * U - 1] >> 24;
-        first_l = cb.b[0] & 0xFFu;
     }
     from_prev = __shfl_sync(kFull, last_h, (lane + 31) & 31);
-    from_next = __shfl_sync(kFull, first_l, (lane + 1) & 31);
-    // lane 0: vector u's left neighbour is lane 31's vector u-1; lane 31:
-    // vector u's right neighbour is lane 0's vector u+1; the halo at the ends.
+    // lane 0: vector u's left neighbour is lane 31's vector u-1, or the halo
     if (lane == 0) from_prev = (from_prev << 8) | ((halo_prev & 1u) << 7);
+}
+
+template <int U>
+__device__ __forceinline__ void chunk_next_low(const ChunkBits<U> &cb, uint32_t halo_next, int lane,
+                                               uint32_t &from_next) {
+    // Byte u of first_l: byte 0 of l_lo[u] (flag of unit 0 of vector u).
+    uint32_t first_l;
+    if constexpr (U == 4) {
+        first_l = prmt(prmt(cb.b[0], cb.b[2], 0x0040), prmt(cb.b[4], cb.b[6], 0x0040), 0x5410);
+    } else if constexpr (U == 2) {
+        first_l = prmt(cb.b[0], cb.b[2], 0x0040) & 0xFFFFu;
+    } else {
+        first_l = cb.b[0] & 0xFFu;
+    }
+    from_next = __shfl_sync(kFull, first_l, (lane + 1) & 31);
+    // lane 31: vector u's right neighbour is lane 0's vector u+1, or the halo
     if (lane == 31) from_next = (from_next >> 8) | ((halo_next & 1u) << (8 * U - 1));
+}
+
+template <int U>
+__device__ __forceinline__ void chunk_classes(ChunkBits<U> &cb, uint32_t halo_prev, uint32_t halo_next, int lane,
+                                              uint32_t &from_prev, uint32_t &from_next) {
+    chunk_classes_prev<U>(cb, halo_prev, lane, from_prev);
+    chunk_next_low<U>(cb, halo_next, lane, from_next);
+}
+
+// Section 3.1 step two for a whole chunk: in a well-formed run every unit's
+// "left neighbour is high" equals its own "is low".  Returns nonzero in some
+// lane iff that fails at a unit of the chunk or at the unit just after it
+// (the halo, whose left neighbour is the chunk's last unit), i.e. iff the
+// chunk holds a mismatched unit or its first unit is low without a high
+// before it (the mismatch then belongs to the previous chunk).
+template <int U>
+__device__ __forceinline__ uint32_t chunk_step_two(const ChunkBits<U> &cb, uint32_t from_prev, uint32_t halo_next,
+                                                   int lane) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t h_lo = cb.a[2 * u], h_hi = cb.a[2 * u + 1];
+        const uint32_t pin = (from_prev << (24 - 8 * u)) & 0x80000000u;
+        x |= (__funnelshift_l(pin, h_lo, 8) ^ cb.b[2 * u]) | (__funnelshift_l(h_lo, h_hi, 8) ^ cb.b[2 * u + 1]);
+    }
+    if (lane == 31) x |= (cb.a[2 * U - 1] >> 31) ^ (halo_next & 1u);
+    return x;
 }
 
 // Mismatch flags of vector u of the chunk (Section 1 rule, Section 3.1 step

@@ -185,6 +185,7 @@ struct BatchSlot {
     int64_t strings = 0;     // strings of the launched batch (requests plus padding strings)
     int64_t desc_off = 0;    // byte offset of the direct-request descriptors in the head region
     int ndirect = 0;
+    int64_t unit_cap = 0;    // units the batch's arena space holds after the head region
     std::vector<int> req_of_string;  // request index of each string, -1 for padding
     cudaEvent_t ev_h2d = nullptr, ev_kernel = nullptr, ev_done = nullptr;
     int status = UTF16_OK;
@@ -281,6 +282,11 @@ static void launch_batch_slot(utf16_server *S, int si) {
     b.strings = strings;
     b.ndirect = nd;
     b.status = UTF16_OK;
+    if (pos > b.unit_cap) {  // admission reserves an upper bound of this layout; never launch past it
+        b.status = UTF16_ENOMEM;
+        cudaEventRecord(b.ev_done, S->s_d2h);
+        return;
+    }
 
     cudaError_t e = cudaMemcpyAsync(b.d_offsets, h_off, (size_t)(strings + 1) * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, S->s_h2d);
@@ -341,7 +347,11 @@ static void scheduler_main(utf16_server *S) {
         b.reqs.clear();
         // Admission in arrival order: stop at the first request that does not
         // fit (keeps FIFO order; a later, smaller request does not overtake).
-        int64_t nreq = 0, pieces = 0, small_units = 0, units = 0, bytes = 0, need = 0;
+        // The launch packs staged requests first and then each aligned one
+        // (large or direct) at a 16-byte aligned offset, so the units needed
+        // are at most the staged units plus, per aligned request, its units
+        // and 7 units of padding.
+        int64_t nreq = 0, pieces = 0, small_units = 0, aligned_units = 0, bytes = 0, need = 0;
         int64_t first_off = 0, head = 0, desc_off = 0;
         while (!S->pending.empty()) {
             Request &r = S->pending.front();
@@ -356,8 +366,9 @@ static void scheduler_main(utf16_server *S) {
             }
             const bool large = r.n * 2 >= o.small_request_bytes;
             const bool aligned = large || r.direct;
-            const int64_t u2 = (aligned ? align_up(units, 8) : units) + r.n;
             const int64_t sm2 = small_units + (aligned ? 0 : r.n);
+            const int64_t al2 = aligned_units + (aligned ? r.n + 7 : 0);
+            const int64_t u2 = sm2 + al2;
             int64_t f2, h2, d2;
             r.large = large;
             batch_head_layout(nreq + 1, pieces + pieces_of(r), f2, h2, &d2);
@@ -367,8 +378,8 @@ static void scheduler_main(utf16_server *S) {
                 break;
             nreq += 1;
             pieces += pieces_of(r);
-            units = u2;
             small_units = sm2;
+            aligned_units = al2;
             bytes += r.n * 2;
             need = need2;
             first_off = f2;
@@ -403,6 +414,7 @@ static void scheduler_main(utf16_server *S) {
         b.d_first = (long long *)(base + first_off);
         b.d_desc = (CopyDesc *)(base + desc_off);
         b.d_units = (uint16_t *)(base + head);
+        b.unit_cap = (need - head) / 2;
         S->stats.batches++;
         S->stats.max_batch_requests = std::max(S->stats.max_batch_requests, nreq);
         lk.unlock();

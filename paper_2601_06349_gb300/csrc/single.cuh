@@ -120,7 +120,14 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
 
     // Slow path: locate the mismatched units.
     uint32_t from_prev, from_next;
-    chunk_classes<U>(cb, unit_is_high(ch.halo), unit_is_low(ch.halo), lane, from_prev, from_next);
+    chunk_classes_prev<U>(cb, unit_is_high(ch.halo), lane, from_prev);
+    if constexpr (MODE == kModeCheck) {
+        // Read-only check: the step-two test clears chunks whose surrogates
+        // all pair up, without locating anything (chunks at the string ends
+        // take the full path).
+        if (!edge && !__any_sync(kFull, chunk_step_two<U>(cb, from_prev, unit_is_low(ch.halo), lane) != 0)) return;
+    }
+    chunk_next_low<U>(cb, unit_is_low(ch.halo), lane, from_next);
     bool found = false;
     uint32_t any_bad = 0;
 #pragma unroll

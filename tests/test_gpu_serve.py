@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import workloads
+from gpu_util import first_diff
 
 pytestmark = pytest.mark.gpu
 
@@ -118,7 +119,8 @@ def test_pinned_and_pageable_in_one_batch(pkg):
     assert st["max_batch_requests"] > 10
     for i, (w, f) in enumerate(want):
         got = outs[i] if isinstance(outs[i], np.ndarray) else outs[i].numpy().view(np.uint16)
-        assert np.array_equal(got, w) and fb[i] == f, i
+        assert np.array_equal(got, w), (i, first_diff(got, w))
+        assert fb[i] == f, (i, fb[i], f)
 
 
 def test_injected_admission_failures_leave_others_exact(pkg):
@@ -180,3 +182,34 @@ def test_oversize_request_rejected(pkg):
         big = np.zeros(1 << 20, np.uint16)
         with pytest.raises(pkg.Utf16Error):
             srv.submit(big, big)
+
+
+def test_aligned_padding_fits_reservation(pkg):
+    """Admission reserves arena space for the launch layout, where staged
+    requests are packed first and every directly copied request starts at a
+    16-byte boundary.  Alternating direct requests of 8k+1 units with staged
+    ones of 8k+7 units makes that layout much longer than the arrival-order
+    one; every request must still come back exact."""
+    import torch
+    rng = np.random.default_rng(29)
+    reqs = []
+    for i in range(400):
+        n = int(8 * rng.integers(0, 40) + (1 if i % 2 == 0 else 7))
+        u = workloads.mixed(n, 1e-2, seed=2900 + i)
+        reqs.append(u)
+    want = _expect(reqs)
+    for rep in range(3):
+        ins, outs = [], []
+        for i, u in enumerate(reqs):
+            if i % 2 == 1:
+                ins.append(u.copy())
+                outs.append(np.zeros_like(u))
+            else:
+                ins.append(torch.from_numpy(u.view(np.int16).copy()).pin_memory())
+                outs.append(torch.zeros(u.size, dtype=torch.int16).pin_memory())
+        with pkg.Server(max_inflight_batches=2, direct_host_access=1, hbm_budget_bytes=64 << 20) as srv:
+            _, fb = srv.replay(ins, outs, rate_per_s=0, seed=rep)
+        for i, (w, f) in enumerate(want):
+            got = outs[i] if isinstance(outs[i], np.ndarray) else outs[i].numpy().view(np.uint16)
+            assert fb[i] == f, (rep, i, fb[i], f)
+            assert np.array_equal(got, w), (rep, i, first_diff(got, w))

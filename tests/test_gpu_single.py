@@ -223,3 +223,55 @@ def test_raw_c_abi_host_first_bad_pointer(pkg):
     rc = pkg.lib().utf16_to_well_formed_first_bad(d.data_ptr(), out.data_ptr(), u.size, ctypes.addressof(w), None)
     assert rc == 0 and w.value == v.value
     assert np.array_equal(to_host(out), oracle.to_well_formed(u))
+
+
+def _plant(base, edge, kind):
+    """One mismatch next to unit `edge` of a string of non-surrogates and
+    pairs (with a neighbour or two rewritten so that it stays the only one
+    nearby)."""
+    u = base.copy()
+    u[edge - 3:edge + 3] = 0x41
+    if 0xD800 <= u[edge - 4] <= 0xDBFF:  # its low was overwritten
+        u[edge - 4] = 0x42
+    if 0xDC00 <= u[edge + 3] <= 0xDFFF:  # its high was overwritten
+        u[edge + 3] = 0x42
+    if kind == "lone_high_last":       # last unit of the chunk before `edge`: a high with no low after it
+        u[edge - 1] = 0xD800
+    elif kind == "lone_low_first":     # first unit of the chunk: a low with no high before it
+        u[edge] = 0xDC00
+    elif kind == "pair_across":        # a valid pair across the chunk edge (no mismatch at all)
+        u[edge - 1], u[edge] = 0xD83D, 0xDE0A
+    elif kind == "lone_high_first":
+        u[edge] = 0xDBFF
+    elif kind == "lone_low_last":
+        u[edge - 1] = 0xDFFF
+    return u
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("units_per_thread", [2, 4])
+def test_check_mismatch_at_chunk_edges(pkg, variant, units_per_thread):
+    """The read-only check clears whole chunks with the step-two test; a
+    mismatch in a chunk's first or last unit (the last one is only visible
+    through the unit after the chunk) must still be found, and a pair across
+    two chunks must not be reported."""
+    chunk_units = 256 * units_per_thread
+    base = workloads.mixed(300_000, 0.0, seed=61)
+    saved = pkg.get_config()
+    pkg.set_config(check_variant=variant, single_units_per_thread=units_per_thread)
+    try:
+        for a in (0, 5):
+            for k in (3, 101):
+                edge = k * chunk_units - a  # first unit of warp chunk k for a string misaligned by a units
+                for kind in ("lone_high_last", "lone_low_first", "pair_across", "lone_high_first", "lone_low_last"):
+                    u = _plant(base, edge, kind)
+                    want = oracle.first_bad(u)
+                    if kind == "pair_across":
+                        assert want == u.size
+                    else:
+                        assert edge - 1 <= want <= edge, (kind, want, edge)
+                    g = Guarded(u.size, a, u)
+                    assert pkg.first_error_index_sync(g.view) == want, (variant, units_per_thread, a, k, kind)
+                    assert int(pkg.first_error_index(g.view).item()) == want, (variant, units_per_thread, a, k, kind)
+    finally:
+        pkg.set_config(saved)
