@@ -148,6 +148,19 @@ int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64
                                int64_t *first_bad, utf16_stream_t stream);
 
 /*
+ * Validates a ragged batch's offsets, which the batch entry points above
+ * take on trust: *first_violation = the smallest i in [0, num_strings] with
+ * offsets[0] < 0 (i = 0) or offsets[i] < offsets[i-1] (i > 0), or -1 when the
+ * array is valid.  One read of the array (8 bytes per string).
+ *   offsets          [num_strings + 1] int64, DEVICE, 8-byte aligned
+ *   first_violation  host pointer: the call waits for the stream and returns
+ *                    the value; device pointer: written in stream order
+ * Returns UTF16_EINVAL for a null pointer or negative num_strings.
+ */
+int utf16_check_offsets(const int64_t *offsets, int64_t num_strings, int64_t *first_violation,
+                        utf16_stream_t stream);
+
+/*
  * toWellFormed plus first-error index on HOST buffers.  The string is cut
  * into chunks that are copied to the device, repaired and copied back on
  * three library-owned streams so that the two copy directions and the kernel

@@ -87,6 +87,7 @@ def _declare(lib):
         "utf16_get_tuned": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_set_tuned": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_error_positions": ([vp, i64, vp, i64, vp, vp], ctypes.c_int),
+        "utf16_check_offsets": ([vp, i64, vp, vp], ctypes.c_int),
         "utf16_selftest_bounded_wait": ([i64], ctypes.c_int),
         "utf16_to_well_formed_first_bad_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "utf16_release_device": ([], ctypes.c_int),
@@ -291,6 +292,18 @@ def first_error_index_batch(units, offsets, first_bad=None, *, stream=None):
         _check(lib().utf16_is_well_formed_batch(units.data_ptr(), offsets.data_ptr(), count, first_bad.data_ptr(),
                                                 _stream(stream, units.device)), "utf16_is_well_formed_batch")
     return first_bad
+
+
+def check_offsets(offsets, *, stream=None) -> int:
+    """Smallest index violating "offsets[0] >= 0 and non-decreasing" of a
+    device int64 offsets tensor, or -1 when it is valid (waits for the
+    stream)."""
+    _offsets(offsets)
+    out = ctypes.c_int64(0)
+    with _torch().cuda.device(offsets.device):
+        _check(lib().utf16_check_offsets(offsets.data_ptr(), offsets.numel() - 1, ctypes.byref(out),
+                                         _stream(stream, offsets.device)), "utf16_check_offsets")
+    return out.value
 
 
 def to_well_formed_host(host_in, host_out=None):

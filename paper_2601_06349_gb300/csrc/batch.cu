@@ -15,9 +15,13 @@
 //   - slow path: the warp finds the first string starting at or after the
 //     chunk by a 32-way search over `offsets` (a window of 32 consecutive
 //     entries from the previous chunk's answer first), marks every string
-//     start inside the chunk in a per-warp bitmask in shared memory, and
+//     start inside the chunk in a per-warp byte map in shared memory, and
 //     applies the pairing rule with "no left neighbour" at a start and "no
-//     right neighbour" just before one.
+//     right neighbour" just before one;
+//   - per-string first-error index: the chunk's mismatch bits go to shared
+//     memory (one byte per vector, plus a one-bit-per-byte summary from a
+//     ballot), then each lane takes one string of the offsets window and
+//     finds the first set bit from its start.
 #include <cuda_runtime.h>
 #include <limits.h>
 
@@ -128,9 +132,29 @@ __device__ __forceinline__ void batch_store_vec(uint16_t *d, const uint4 &f, boo
 template <int U>
 struct __align__(16) WarpScratch {
     uint8_t starts[U * kWarpSliceUnits + 16];  // 0x80 at r when a string starts at unit cfirst + r (r <= CU)
-    long long win[32];                          // offsets[base .. base + 31]: the chunk's first window
-    long long win_prev;                         // offsets[base - 1], or LLONG_MIN
+    uint8_t bad[U * 32];                        // per-string first-error modes: mismatch bits of vector 32u + lane
 };
+
+// Per-string first-error modes: the chunk's mismatched units as one bit per
+// unit (ws.bad, byte 32u + lane = vector u of that lane, bit k = unit k)
+// plus a summary with one bit per byte (bit lane of nz[u]).  Returns the
+// first unit index >= r (0 <= r < CU) of the chunk with its bit set, or CU.
+template <int U>
+__device__ __forceinline__ int first_mismatch_from(const WarpScratch<U> &ws, const uint32_t (&nz)[U], int r) {
+    const int b0 = r >> 3;
+    const uint32_t m0 = ws.bad[b0] & (0xFFu << (r & 7));
+    if (m0) return (b0 << 3) + __ffs(m0) - 1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int from = b0 + 1 - 32 * u;  // first byte of word u after byte b0
+        uint32_t m = from >= 32 ? 0u : from > 0 ? nz[u] & (0xFFFFFFFFu << from) : nz[u];
+        if (m) {
+            const int b = 32 * u + __ffs(m) - 1;
+            return (b << 3) + __ffs(ws.bad[b]) - 1;
+        }
+    }
+    return U * kWarpSliceUnits;
+}
 
 template <int MODE, int ST, int U>
 __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long long cfirst, long long lo, long long hi,
@@ -169,21 +193,17 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
         off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
         ge = __ballot_sync(kFull, off >= cfirst);
     }
-    const long long s_first = base + __ffs(ge) - 1;  // first string starting at or after cfirst
-    const long long base_first = base;                 // ws.win holds offsets[base_first ..]
+    const int fs_lane = __ffs(ge) - 1;
+    const long long s_first = base + fs_lane;  // first string starting at or after cfirst
+    const long long base_first = base;
+    const long long off_first = off;           // offsets[base_first + lane]
     hint = s_first;
     bool simple = true;  // all starts of the chunk lie in the first window
-    if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
-        ws.win[lane] = off;
-        if (lane == 0) ws.win_prev = base > 0 ? A.offsets[base - 1] : LLONG_MIN;
-    }
-    long long s_last = s_first - 1;  // last string index starting in the chunk
     __syncwarp();
-    for (int w = 0;; ++w) {
+    for (;;) {
         const bool inside = off >= cfirst && off <= cend;
         if (inside) ws.starts[off - cfirst] = 0x80;
         const unsigned m = __ballot_sync(kFull, inside);
-        if (m) s_last = base + 31 - __clz(m);
         // continue while the window's last entry still starts inside the chunk
         if (!(m >> 31)) break;
         simple = false;
@@ -194,8 +214,7 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
     __syncwarp();
     uint32_t from_prev, from_next;
     chunk_classes<U>(cb, unit_is_high(ch.halo), unit_is_low(ch.halo), lane, from_prev, from_next);
-    long long prev_s = -1;
-    const long long s_lo = hint > 0 ? hint - 1 : 0;
+    uint32_t nz[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int r0 = u * kWarpSliceUnits + lane * kUnitsPerVec;
@@ -221,47 +240,45 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
                                           hi, gather4(bad_lo) | (gather4(bad_hi) << 4));
         }
         if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
-            // Per-string first-error index: the first bad unit of each string
-            // within this thread's units, one atomic per (thread, string).
-            uint32_t rest = gather4(bad_lo) | (gather4(bad_hi) << 4);
-            while (rest) {
-                const int b = __ffs(rest) - 1;
-                rest &= rest - 1;
-                const long long p = p0 + b;
-                long long a_i, start;
-                if (simple) {
-                    // largest window index whose offset is <= p (empty strings
-                    // share offsets; the last of them is the one holding p)
-                    int wa = -1, wb = 31;
-                    while (wa < wb) {
-                        const int mid = (wa + wb + 1) >> 1;
-                        if (ws.win[mid] <= p)
-                            wa = mid;
-                        else
-                            wb = mid - 1;
-                    }
-                    a_i = base_first + wa;
-                    start = wa >= 0 ? ws.win[wa] : ws.win_prev;
-                } else {
-                    a_i = s_lo;
-                    long long b_i = s_last > s_lo ? s_last : s_lo;
-                    while (a_i < b_i) {  // largest index with offsets[index] <= p
-                        const long long mid = (a_i + b_i + 1) >> 1;
-                        if (A.offsets[mid] <= p)
-                            a_i = mid;
-                        else
-                            b_i = mid - 1;
-                    }
-                    start = -1;
-                }
-                if (a_i > A.count - 1) a_i = A.count - 1;
-                if (a_i < 0) a_i = 0;
-                if (a_i != prev_s) {
-                    prev_s = a_i;
-                    if (start < 0 || start == LLONG_MIN) start = A.offsets[a_i];
-                    atomicMin(&A.first_bad[a_i], p - start);
-                }
+            const uint32_t bits8 = gather4(bad_lo) | (gather4(bad_hi) << 4);
+            ws.bad[u * 32 + lane] = (uint8_t)bits8;
+            nz[u] = __ballot_sync(kFull, bits8 != 0);
+        }
+    }
+    if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
+        uint32_t any = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) any |= nz[u];
+        if (any == 0) return;
+        __syncwarp();
+        // Per-string first-error index, one lane per string: the string of
+        // window entry `lane` starts at `off` and ends at the next entry; its
+        // first mismatched unit in this chunk is the first set bit from its
+        // start.  Strings that start in this chunk take the window entries in
+        // [cfirst, cend); the string holding the chunk's first units (it
+        // started earlier) takes the units before the first of them.
+        const int q0 = first_mismatch_from<U>(ws, nz, 0);
+        const long long first_start = __shfl_sync(kFull, off_first, fs_lane);  // offsets[s_first]
+        const long long before = __shfl_sync(kFull, off_first, fs_lane >= 1 ? fs_lane - 1 : 0);
+        if (lane == 0 && s_first >= 1 && s_first <= A.count && q0 < (int)CU && cfirst + q0 < first_start) {
+            const long long start = fs_lane >= 1 ? before : A.offsets[s_first - 1];
+            atomicMin(&A.first_bad[s_first - 1], cfirst + q0 - start);
+        }
+        long long wbase = base_first;
+        long long woff = off_first;
+        for (;;) {
+            const long long wnext = __shfl_down_sync(kFull, woff, 1);
+            const long long widx = wbase + lane;
+            const bool starts_here = woff >= cfirst && woff < cend && widx < A.count;
+            if (starts_here) {
+                const long long end = lane < 31 ? wnext : A.offsets[widx + 1];
+                const int q = first_mismatch_from<U>(ws, nz, (int)(woff - cfirst));
+                if (cfirst + q < end && q < (int)CU) atomicMin(&A.first_bad[widx], cfirst + q - woff);
             }
+            if (simple || !__shfl_sync(kFull, starts_here ? 1 : 0, 31)) break;
+            wbase += 32;
+            const long long ni = wbase + lane;
+            woff = ni <= A.count ? A.offsets[ni] : LLONG_MAX;
         }
     }
 }

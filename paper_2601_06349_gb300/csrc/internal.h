@@ -66,6 +66,11 @@ struct BatchLaunch {
 cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream);
 const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch = false);
 
+// Smallest index violating "offsets[0] >= 0, non-decreasing" (or -1) into
+// *result, through the stream's slot.
+cudaError_t launch_check_offsets(const long long *offsets, long long count, Slot *slot, long long *result,
+                                 int max_blocks, cudaStream_t stream);
+
 // Initialise a pool of scratch slots (min = all ones, done = 0).
 cudaError_t init_slots(Slot *slots, int count, cudaStream_t stream);
 

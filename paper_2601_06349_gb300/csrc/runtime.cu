@@ -470,4 +470,31 @@ int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64
     return run_batch(in, nullptr, offsets, num_strings, kModeCheck, first_bad, (cudaStream_t)stream);
 }
 
+int utf16_check_offsets(const int64_t *offsets, int64_t num_strings, int64_t *first_violation,
+                        utf16_stream_t stream) {
+    if (num_strings < 0 || !offsets || !first_violation || ((uintptr_t)offsets & 7u)) return UTF16_EINVAL;
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool on_device = is_device_ptr(first_violation);
+    Slot *slot = nullptr;
+    rc = ctx->slot_for(s, &slot);
+    if (rc) return rc;
+    long long *res = on_device ? (long long *)first_violation : &slot->result;
+    if (launch_check_offsets((const long long *)offsets, num_strings, slot, res, ctx->sms * 8, s) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    if (!on_device) {
+        if (cudaMemcpyAsync(first_violation, &slot->result, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+    }
+    return UTF16_OK;
+}
+
 }  // extern "C"

@@ -112,3 +112,37 @@ def test_batch_boundary_pairs(pkg):
     lens = np.array([2, 1, 3] * 1000, np.int64)  # splits the first pair, keeps the second
     offs = workloads.offsets_from_lengths(lens)
     _run_all_forms(pkg, u, offs, 0, 0, "boundary pairs")
+
+
+def test_check_offsets(pkg):
+    """utf16_check_offsets reports the smallest index that breaks
+    "offsets[0] >= 0, non-decreasing", or -1, for host and device results."""
+    import ctypes
+    import torch
+    lens = workloads.lognormal_lengths(200_000, seed=71)
+    good = workloads.offsets_from_lengths(lens.astype(np.int64), start=5)
+    d = torch.from_numpy(good).cuda()
+    assert pkg.check_offsets(d) == -1
+    assert pkg.check_offsets(d[:1]) == -1  # no strings
+    cases = {0: None, 1: None, 777: None, 123_456: None, good.size - 1: None}
+    for i in cases:
+        bad = good.copy()
+        if i == 0:
+            bad[0] = -1
+        else:
+            bad[i] = bad[i - 1] - 1
+        assert pkg.check_offsets(torch.from_numpy(bad).cuda()) == i, i
+    two = good.copy()
+    two[500] = two[499] - 3
+    two[90_000] = -7
+    assert pkg.check_offsets(torch.from_numpy(two).cuda()) == 500
+    res = torch.full((1,), 99, dtype=torch.int64, device="cuda")  # device result, stream ordered
+    s = torch.cuda.current_stream()
+    assert pkg.lib().utf16_check_offsets(torch.from_numpy(two).cuda().data_ptr(), two.size - 1, res.data_ptr(),
+                                         ctypes.c_void_p(s.cuda_stream)) == 0
+    assert int(res.item()) == 500
+    # every entry point of the batch path keeps working after a check on the same stream
+    units = workloads.mixed(int(good[-1]), 1e-2, seed=72)
+    out = pkg.to_well_formed_batch(torch.from_numpy(units.view(np.int16)).cuda(), d)
+    lo, hi = int(good[0]), int(good[-1])
+    assert np.array_equal(out.cpu().numpy().view(np.uint16)[lo:hi], oracle.to_well_formed_batch(units, good)[lo:hi])
