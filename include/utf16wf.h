@@ -211,6 +211,7 @@ typedef struct {
     int check_variant;           /* read-only check (utf16_is_well_formed): 0, 1 or 2 as single_variant */
     int inplace_unit_stores;     /* in-place repair of single strings: 0 = store each 16-byte block that
                                     holds a replaced unit, 1 = store only the replaced units (2 bytes) */
+    int inplace_variant;         /* in-place repair of single strings: 0, 1 or 2 as single_variant */
 } utf16_config;
 
 /* Default configuration of the current device (used where nothing is tuned). */
@@ -224,7 +225,9 @@ int utf16_set_config(const utf16_config *cfg);
  * x blocks per SM) on the caller's own device buffers with CUDA events,
  * `reps` launches each after one warm-up, on a library stream; synchronous.
  * The fastest is stored for the size bucket floor(log2(n)) of single strings
- * (utf16_autotune_single, out-of-place repair with first-error index) or for
+ * (utf16_autotune_single: out-of-place repair with first-error index; then
+ * the data path of the read-only check, timed over the whole string as for a
+ * well-formed one, and of in-place repair, timed on copies of `in`) or for
  * the bucket floor(log2(num_strings)) of batches (utf16_autotune_batch, the
  * out-of-place batch repair), and used by later calls in that bucket.
  *   out   scratch output of the same size as in (written).

@@ -36,7 +36,8 @@ class Config(ctypes.Structure):
     _fields_ = [("single_variant", ctypes.c_int), ("single_units_per_thread", ctypes.c_int),
                 ("single_blocks_per_sm", ctypes.c_int), ("batch_units_per_thread", ctypes.c_int),
                 ("batch_prefetch", ctypes.c_int), ("batch_blocks_per_sm", ctypes.c_int),
-                ("check_variant", ctypes.c_int), ("inplace_unit_stores", ctypes.c_int)]
+                ("check_variant", ctypes.c_int), ("inplace_unit_stores", ctypes.c_int),
+                ("inplace_variant", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

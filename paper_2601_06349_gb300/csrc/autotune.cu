@@ -100,7 +100,9 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             }
         }
     }
-    // The read-only check separately: each data path with the winner's other settings.
+    // The read-only check separately: each data path with the winner's other
+    // settings, over the whole string (no early exit at the first mismatch, so
+    // that the time is that of a well-formed string of this size).
     float best_check = 1e30f;
     for (int variant = 0; variant <= 2; ++variant) {
         utf16_config c = winner;
@@ -113,6 +115,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
         configure_single(ctx, c, L);
         L.slot = slot;
         L.result = &slot->result;
+        L.full_pass = true;
         if (launch_single(L, t.s) != cudaSuccess) {
             cudaGetLastError();
             return UTF16_ECUDA;
@@ -129,6 +132,46 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
         if (ms < best_check) {
             best_check = ms;
             winner.check_variant = variant;
+        }
+    }
+    // In-place repair: each data path on a fresh copy of `in` in `out` per
+    // launch; the copies alone are timed too and subtracted.
+    {
+        const size_t bytes = (size_t)n * 2u;
+        auto timed = [&](const SingleLaunch *L, float *ms) -> bool {
+            cudaEventRecord(t.a, t.s);
+            for (int r = 0; r < reps; ++r) {
+                if (cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, t.s) != cudaSuccess) return false;
+                if (L && launch_single(*L, t.s) != cudaSuccess) return false;
+            }
+            cudaEventRecord(t.b, t.s);
+            if (cudaEventSynchronize(t.b) != cudaSuccess) return false;
+            return cudaEventElapsedTime(ms, t.a, t.b) == cudaSuccess;
+        };
+        float copies = 0.f;
+        if (!timed(nullptr, &copies)) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+        float best_inplace = 1e30f;
+        for (int variant = 0; variant <= 2; ++variant) {
+            utf16_config c = winner;
+            c.inplace_variant = variant;
+            SingleLaunch L;
+            L.in = out;
+            L.out = out;
+            L.n = n;
+            L.mode = kModeInPlace;
+            configure_single(ctx, c, L);
+            float ms = 0.f;
+            if (!timed(&L, &ms)) {
+                cudaGetLastError();
+                return UTF16_ECUDA;
+            }
+            if (ms - copies < best_inplace) {
+                best_inplace = ms - copies;
+                winner.inplace_variant = variant;
+            }
         }
     }
     {

@@ -42,6 +42,7 @@ struct SingleLaunch {
     bool unit_stores = false;      // in place: 2-byte stores of the replaced units instead of 16-byte blocks
     long long *positions = nullptr;  // kModeList: output array
     long long capacity = 0;          // kModeList: its length
+    bool full_pass = false;          // kModeCheck: read the whole string (no early exit), for timing
 };
 
 cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream);

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
             c += nwarps;
             unsigned long long g = ~0ull;
             if constexpr (MODE == kModeCheck) {
-                if (lane == 0) g = *((volatile unsigned long long *)&A.slot->min);
+                if (lane == 0 && !A.full_pass) g = *((volatile unsigned long long *)&A.slot->min);
             }
             if (c < A.chunks) load_chunk<MODE, U>(A, vin, c, lane, nv);
             const long long cfirst = cur * CU - A.a;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
             const long long cfirst = c * CU - A.a;
             unsigned long long g = ~0ull;
             if constexpr (MODE == kModeCheck) {
-                if (lane == 0) g = *((volatile unsigned long long *)&A.slot->min);
+                if (lane == 0 && !A.full_pass) g = *((volatile unsigned long long *)&A.slot->min);
             }
             Chunk<U> v;
             load_chunk<MODE, U>(A, vin, c, lane, v);
@@ -127,6 +127,7 @@ SingleArgs make_single_args(const SingleLaunch &L, int units_per_chunk) {
     A.unit_stores = L.unit_stores ? 1 : 0;
     A.positions = L.positions;
     A.capacity = L.capacity;
+    A.full_pass = L.full_pass ? 1 : 0;
     return A;
 }
 

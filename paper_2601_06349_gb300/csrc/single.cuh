@@ -23,6 +23,7 @@ struct SingleArgs {
     int unit_stores;     // in place: store replaced units one by one (2 bytes) instead of their 16-byte block
     long long *positions;  // list mode: positions of mismatched units (unordered), `capacity` entries
     long long capacity;
+    int full_pass;         // check: no early exit (the autotuner times a whole pass)
 };
 
 SingleArgs make_single_args(const SingleLaunch &L, int units_per_chunk);

@@ -185,8 +185,10 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
         const uint16_t *stage_units = reinterpret_cast<const uint16_t *>(stage);
         bool skip = false;
         if constexpr (MODE == kModeCheck) {
-            const unsigned long long g = *((volatile unsigned long long *)&A.slot->min);
-            skip = (g != ~0ull && (long long)g < tile_first);
+            if (!A.full_pass) {
+                const unsigned long long g = *((volatile unsigned long long *)&A.slot->min);
+                skip = (g != ~0ull && (long long)g < tile_first);
+            }
         }
         if (!skip) {
             Chunk<kTmaU> ch;
@@ -206,7 +208,8 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
             bool go = next < my_tiles;
             if constexpr (MODE == kModeCheck) {
                 const unsigned long long g = *((volatile unsigned long long *)&A.slot->min);
-                if (g != ~0ull && (long long)g < (first_tile + next * gridDim.x) * kTileUnits - A.a) go = false;
+                if (!A.full_pass && g != ~0ull && (long long)g < (first_tile + next * gridDim.x) * kTileUnits - A.a)
+                    go = false;
             }
             if (go) {
                 issue(next);

@@ -63,9 +63,10 @@ def test_error_positions_small_sweep(pkg):
         assert np.array_equal(np.sort(pos.cpu().numpy()), want), n
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("name,u", list(_cases()))
-def test_in_place_unit_stores(pkg, name, u):
-    pkg.set_config(inplace_unit_stores=1, single_variant=0)
+def test_in_place_unit_stores(pkg, name, u, variant):
+    pkg.set_config(inplace_unit_stores=1, inplace_variant=variant)
     want = oracle.to_well_formed(u)
     for a in (0, 7):
         g = Guarded(u.size, a, u)

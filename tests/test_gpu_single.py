@@ -275,3 +275,29 @@ def test_check_mismatch_at_chunk_edges(pkg, variant, units_per_thread):
                     assert int(pkg.first_error_index(g.view).item()) == want, (variant, units_per_thread, a, k, kind)
     finally:
         pkg.set_config(saved)
+
+
+def test_bench_launch_configuration_full_size(pkg):
+    """The benchmarked step in the launch configuration the bench uses: the
+    autotuner's choice for the 1 GiB string at 1e-2 lone surrogates, then the
+    fused repair, the check and in-place repair, each against the oracle."""
+    import torch
+    u = workloads.large_mixed(1e-2)
+    want = oracle.to_well_formed_threads(u)
+    want_fb = oracle.first_bad_threads(u)
+    saved = pkg.get_config()
+    try:
+        d_in = to_dev(u)
+        d_out = torch.empty_like(d_in)
+        cfg = pkg.autotune_single(d_in, d_out, reps=2)
+        _, fb = pkg.to_well_formed_first_bad(d_in, d_out)
+        got = to_host(d_out)
+        assert np.array_equal(got, want), (cfg.as_dict(), first_diff(got, want))
+        assert int(fb.item()) == want_fb
+        assert pkg.first_error_index_sync(d_in) == want_fb
+        pkg.to_well_formed_(d_in)
+        assert np.array_equal(to_host(d_in), want), cfg.as_dict()
+        del d_in, d_out
+        torch.cuda.empty_cache()
+    finally:
+        pkg.set_config(saved)

@@ -44,7 +44,7 @@ def strings():
 def test_single_configurations(pkg, strings, variant, u, bps):
     import torch
     pkg.set_config(single_variant=variant, single_units_per_thread=u, single_blocks_per_sm=bps,
-                   check_variant=variant)
+                   check_variant=variant, inplace_variant=variant)
     for name, (src, want, want_fb) in strings.items():
         for a_in, a_out in ((0, 0), (3, 3), (5, 1)):
             gi = Guarded(src.size, a_in, src)
