@@ -161,13 +161,15 @@ int utf16_check_offsets(const int64_t *offsets, int64_t num_strings, int64_t *fi
                         utf16_stream_t stream);
 
 /*
- * toWellFormed plus first-error index on HOST buffers.  The string is cut
- * into chunks that are copied to the device, repaired and copied back on
- * three library-owned streams so that the two copy directions and the kernel
- * overlap; each chunk receives its outside neighbours from the host buffer,
- * so the result is that of the whole string.  Blocking: returns when host_out
- * holds the result.  Pinned (page-locked) host buffers give full overlap;
- * pageable ones work but serialise the copies.
+ * toWellFormed plus first-error index on HOST buffers.  Blocking: returns
+ * when host_out holds the result.
+ * When both buffers are page-locked (cudaHostAlloc / cudaHostRegister), one
+ * pass of the fused kernel reads and writes them over the host link
+ * directly.  Otherwise the string is cut into chunks that are copied to the
+ * device, repaired and copied back on three library-owned streams so that
+ * the two copy directions and the kernel overlap; each chunk receives its
+ * outside neighbours from the host buffer, so the result is that of the
+ * whole string (pageable buffers serialise the copies).
  *   host_in, host_out  [n] host; host_out == host_in is allowed.
  *   first_bad_host     one int64_t on the host, or NULL.
  */
@@ -212,6 +214,8 @@ typedef struct {
     int inplace_unit_stores;     /* in-place repair of single strings: 0 = store each 16-byte block that
                                     holds a replaced unit, 1 = store only the replaced units (2 bytes) */
     int inplace_variant;         /* in-place repair of single strings: 0, 1 or 2 as single_variant */
+    int check_blocks_per_sm;     /* read-only check: persistent grid = SMs x this; 0 = as many as fit */
+    int inplace_blocks_per_sm;   /* in-place repair of single strings: the same */
 } utf16_config;
 
 /* Default configuration of the current device (used where nothing is tuned). */
@@ -226,8 +230,9 @@ int utf16_set_config(const utf16_config *cfg);
  * `reps` launches each after one warm-up, on a library stream; synchronous.
  * The fastest is stored for the size bucket floor(log2(n)) of single strings
  * (utf16_autotune_single: out-of-place repair with first-error index; then
- * the data path of the read-only check, timed over the whole string as for a
- * well-formed one, and of in-place repair, timed on copies of `in`) or for
+ * the data path and grid of the read-only check, timed on the repaired
+ * (well-formed) string in `out`, and of in-place repair, timed on copies of
+ * `in`) or for
  * the bucket floor(log2(num_strings)) of batches (utf16_autotune_batch, the
  * out-of-place batch repair), and used by later calls in that bucket.
  *   out   scratch output of the same size as in (written).

@@ -37,7 +37,8 @@ class Config(ctypes.Structure):
                 ("single_blocks_per_sm", ctypes.c_int), ("batch_units_per_thread", ctypes.c_int),
                 ("batch_prefetch", ctypes.c_int), ("batch_blocks_per_sm", ctypes.c_int),
                 ("check_variant", ctypes.c_int), ("inplace_unit_stores", ctypes.c_int),
-                ("inplace_variant", ctypes.c_int)]
+                ("inplace_variant", ctypes.c_int), ("check_blocks_per_sm", ctypes.c_int),
+                ("inplace_blocks_per_sm", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -312,19 +313,15 @@ def to_well_formed_host(host_in, host_out=None):
     ``host_in`` / ``host_out``: CPU tensors of 16-bit units (pinned memory
     gives full copy/compute overlap) or numpy uint16 arrays."""
     import numpy as np
-    if isinstance(host_in, np.ndarray):
-        if host_in.dtype != np.uint16 or not host_in.flags.c_contiguous:
-            raise TypeError("host_in must be a contiguous uint16 array")
-        if host_out is None:
+    if host_out is None:
+        if isinstance(host_in, np.ndarray):
             host_out = np.empty_like(host_in)
-        pin, pout, n = host_in.ctypes.data, host_out.ctypes.data, host_in.size
-    else:
-        torch = _torch()
-        if host_in.is_cuda or host_in.dtype not in (torch.uint16, torch.int16):
-            raise TypeError("host_in must be a CPU tensor of 16-bit units")
-        if host_out is None:
-            host_out = torch.empty_like(host_in, pin_memory=host_in.is_pinned())
-        pin, pout, n = host_in.data_ptr(), host_out.data_ptr(), host_in.numel()
+        else:
+            host_out = _torch().empty_like(host_in, pin_memory=host_in.is_pinned())
+    pin, n = _host_ptr(host_in)
+    pout, n_out = _host_ptr(host_out)
+    if n_out != n:
+        raise ValueError("host_in and host_out lengths differ")
     fb = ctypes.c_int64(-1)
     _check(lib().utf16_to_well_formed_host(ctypes.c_void_p(pin), ctypes.c_void_p(pout), n, ctypes.addressof(fb)),
            "utf16_to_well_formed_host")

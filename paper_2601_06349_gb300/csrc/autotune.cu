@@ -100,15 +100,21 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             }
         }
     }
-    // The read-only check separately: each data path with the winner's other
-    // settings, over the whole string (no early exit at the first mismatch, so
-    // that the time is that of a well-formed string of this size).
+    // The read-only check separately: each data path and grid on `out`, which
+    // now holds the repaired (well-formed) string, so that every candidate
+    // reads the whole string as for valid input (full_pass also turns off the
+    // early exit).
     float best_check = 1e30f;
-    for (int variant = 0; variant <= 2; ++variant) {
+    utf16_config check_winner = winner;
+    for (int variant = 0; variant <= 2; ++variant)
+    for (int bps : block_candidates(ctx->per_sm(single_kernel_for_occupancy(kModeCheck, true, winner.single_units_per_thread,
+                                                                            variant),
+                                                variant == kVariantTma ? single_tma_smem_bytes() : 0))) {
         utf16_config c = winner;
         c.check_variant = variant;
+        c.check_blocks_per_sm = bps;
         SingleLaunch L;
-        L.in = in;
+        L.in = out;
         L.n = n;
         L.mode = kModeCheck;
         L.first_bad = true;
@@ -131,9 +137,11 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
         cudaEventElapsedTime(&ms, t.a, t.b);
         if (ms < best_check) {
             best_check = ms;
-            winner.check_variant = variant;
+            check_winner = c;
         }
     }
+    winner.check_variant = check_winner.check_variant;
+    winner.check_blocks_per_sm = check_winner.check_blocks_per_sm;
     // In-place repair: each data path on a fresh copy of `in` in `out` per
     // launch; the copies alone are timed too and subtracted.
     {
@@ -154,9 +162,14 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             return UTF16_ECUDA;
         }
         float best_inplace = 1e30f;
-        for (int variant = 0; variant <= 2; ++variant) {
+        utf16_config inplace_winner = winner;
+        for (int variant = 0; variant <= 2; ++variant)
+        for (int bps : block_candidates(
+                 ctx->per_sm(single_kernel_for_occupancy(kModeInPlace, false, winner.single_units_per_thread, variant),
+                             variant == kVariantTma ? single_tma_smem_bytes() : 0))) {
             utf16_config c = winner;
             c.inplace_variant = variant;
+            c.inplace_blocks_per_sm = bps;
             SingleLaunch L;
             L.in = out;
             L.out = out;
@@ -170,9 +183,11 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             }
             if (ms - copies < best_inplace) {
                 best_inplace = ms - copies;
-                winner.inplace_variant = variant;
+                inplace_winner = c;
             }
         }
+        winner.inplace_variant = inplace_winner.inplace_variant;
+        winner.inplace_blocks_per_sm = inplace_winner.inplace_blocks_per_sm;
     }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);

@@ -1,10 +1,15 @@
-// toWellFormed plus first-error index on host buffers: chunks of the string
-// go host -> device, are repaired in place in a device staging buffer and go
-// back, on three library-owned streams so that both copy directions and the
-// kernels of different chunks overlap.  Each chunk gets its outside
-// neighbours (the units just before and after it in the whole string) from
-// the host buffer, so the chunked result equals the whole-string result (the
-// rule reads only a unit's immediate neighbours, Section 1).
+// toWellFormed plus first-error index on host buffers.
+//
+// Both buffers page-locked (pinned): one pass of the fused kernel reads the
+// input and writes the output over the host link itself, no staging.
+//
+// Otherwise: chunks of the string go host -> device, are repaired in place in
+// a device staging buffer and go back, on three library-owned streams so
+// that both copy directions and the kernels of different chunks overlap.
+// Each chunk gets its outside neighbours (the units just before and after it
+// in the whole string) from the host buffer, so the chunked result equals the
+// whole-string result (the rule reads only a unit's immediate neighbours,
+// Section 1).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -23,14 +28,20 @@ static int64_t host_chunk_units() {
     return (int64_t)v;
 }
 
-int DeviceCtx::ensure_staging(int64_t units, int64_t chunks) {
-    if (!lanes[0]) {
+static int ensure_lanes(DeviceCtx *ctx) {
+    if (!ctx->lanes[0]) {
         for (int i = 0; i < kHostLanes; ++i)
-            if (cudaStreamCreateWithFlags(&lanes[i], cudaStreamNonBlocking) != cudaSuccess) {
+            if (cudaStreamCreateWithFlags(&ctx->lanes[i], cudaStreamNonBlocking) != cudaSuccess) {
                 cudaGetLastError();
                 return UTF16_ECUDA;
             }
     }
+    return UTF16_OK;
+}
+
+int DeviceCtx::ensure_staging(int64_t units, int64_t chunks) {
+    const int rc = ensure_lanes(this);
+    if (rc) return rc;
     if (stage_units < units) {
         for (int i = 0; i < kHostLanes; ++i) {
             if (stage[i]) cudaFree(stage[i]);
@@ -80,6 +91,52 @@ static bool is_device_memory(const void *p) {
     return at.type == cudaMemoryTypeDevice;
 }
 
+// Device address of `bytes` bytes of page-locked host memory at p, or
+// nullptr when any of them is not page-locked (one mapping end to end).
+static const void *pinned_view(const void *p, int64_t bytes) {
+    cudaPointerAttributes a, b;
+    const char *last = (const char *)p + bytes - 1;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if ((const char *)b.devicePointer - (const char *)a.devicePointer != bytes - 1) return nullptr;
+    return a.devicePointer;
+}
+
+// Both buffers pinned: one fused pass on a library stream.
+static int host_direct(DeviceCtx *ctx, const uint16_t *din, uint16_t *dout, int64_t n, int64_t *first_bad_host) {
+    int rc = ensure_lanes(ctx);
+    if (rc) return rc;
+    cudaStream_t s = ctx->lanes[0];
+    Slot *slot;
+    rc = ctx->slot_for(s, &slot);
+    if (rc) return rc;
+    SingleLaunch L;
+    L.in = din;
+    L.out = dout;
+    L.n = n;
+    L.mode = din == dout ? kModeInPlace : kModeOut;
+    L.first_bad = true;
+    utf16_config cfg = ctx->single_config(n);
+    // Host memory is far: keep the next chunk's loads in flight (and no bulk copies).
+    cfg.single_variant = cfg.inplace_variant = kVariantLdgPrefetch;
+    configure_single(ctx, cfg, L);
+    L.slot = slot;
+    L.result = &slot->result;
+    int64_t fb = n;
+    if (launch_single(L, s) != cudaSuccess ||
+        cudaMemcpyAsync(&fb, &slot->result, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    if (first_bad_host) *first_bad_host = fb;
+    return UTF16_OK;
+}
+
 }  // namespace u16wf
 
 using namespace u16wf;
@@ -102,6 +159,11 @@ extern "C" int utf16_to_well_formed_host(const uint16_t *host_in, uint16_t *host
     if (rc) return rc;
 
     std::lock_guard<std::mutex> lk(ctx->stage_mu);
+    {
+        const void *din = pinned_view(host_in, n * 2);
+        const void *dout = din ? pinned_view(host_out, n * 2) : nullptr;
+        if (din && dout) return host_direct(ctx, (const uint16_t *)din, (uint16_t *)dout, n, first_bad_host);
+    }
     const int64_t chunk = host_chunk_units();
     const int64_t chunks = (n + chunk - 1) / chunk;
     rc = ctx->ensure_staging(n < chunk ? n : chunk, chunks);

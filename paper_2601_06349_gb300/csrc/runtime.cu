@@ -80,7 +80,8 @@ utf16_config DeviceCtx::batch_config(int64_t units, int64_t count) {
 
 static bool config_valid(const utf16_config &c) {
     return c.single_variant >= 0 && c.single_variant <= 2 && c.check_variant >= 0 && c.check_variant <= 2 &&
-           c.inplace_variant >= 0 && c.inplace_variant <= 2 &&
+           c.inplace_variant >= 0 && c.inplace_variant <= 2 && c.check_blocks_per_sm >= 0 &&
+           c.check_blocks_per_sm <= 64 && c.inplace_blocks_per_sm >= 0 && c.inplace_blocks_per_sm <= 64 &&
            (c.inplace_unit_stores == 0 || c.inplace_unit_stores == 1) &&
            (c.single_units_per_thread == 2 || c.single_units_per_thread == 4) && c.single_blocks_per_sm >= 0 &&
            c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
@@ -135,7 +136,12 @@ int get_ctx(DeviceCtx **out) {
     // 0.68 of the copy peak); out of place with the first-error index the
     // plain loads are (0.93 vs 0.89).
     d.inplace_variant = env_int("UTF16WF_INPLACE_VARIANT", kVariantLdgPrefetch);
-    if (!config_valid(d)) d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg, 0, kVariantLdgPrefetch};
+    // The read-only check streams best with 3 resident blocks per SM rather
+    // than all that fit (0.81 vs 0.75 of the copy peak, 1 GiB well-formed string).
+    d.check_blocks_per_sm = env_int("UTF16WF_CHECK_BLOCKS_PER_SM", 3);
+    d.inplace_blocks_per_sm = env_int("UTF16WF_INPLACE_BLOCKS_PER_SM", 0);
+    if (!config_valid(d))
+        d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg, 0, kVariantLdgPrefetch, 3, 0};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);
@@ -153,7 +159,10 @@ void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) 
     const bool tma = L.variant == kVariantTma;
     const void *fn = single_kernel_for_occupancy(L.mode, fb, L.units_per_thread, L.variant);
     const int fit = ctx->per_sm(fn, tma ? single_tma_smem_bytes() : 0);
-    const int per = cfg.single_blocks_per_sm > 0 ? std::min(cfg.single_blocks_per_sm, fit) : fit;
+    const int want = L.mode == kModeCheck     ? cfg.check_blocks_per_sm
+                     : L.mode == kModeInPlace ? cfg.inplace_blocks_per_sm
+                                              : cfg.single_blocks_per_sm;
+    const int per = want > 0 ? std::min(want, fit) : fit;
     L.max_blocks = per * ctx->sms;
 }
 

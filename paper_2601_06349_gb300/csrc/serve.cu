@@ -187,7 +187,9 @@ struct BatchSlot {
     int ndirect = 0;
     int64_t unit_cap = 0;    // units the batch's arena space holds after the head region
     std::vector<int> req_of_string;  // request index of each string, -1 for padding
-    cudaEvent_t ev_h2d = nullptr, ev_kernel = nullptr, ev_done = nullptr;
+    cudaStream_t stream = nullptr;  // the batch's copies in, kernels and copies out, in order
+    cudaEvent_t ev_done = nullptr;
+    uint64_t seq = 0;               // launch sequence number (arena space is freed in this order)
     int status = UTF16_OK;
 };
 
@@ -212,7 +214,6 @@ struct utf16_server {
     u16wf::DeviceCtx *ctx = nullptr;
     char *arena = nullptr;
     std::unique_ptr<u16wf::FifoRing> ring;
-    cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     std::vector<u16wf::BatchSlot> slots;
 
     std::mutex mu;
@@ -220,7 +221,10 @@ struct utf16_server {
     std::condition_variable cv_done;   // completions available
     std::deque<u16wf::Request> pending;
     std::deque<int> free_slots;
-    std::deque<int> inflight;  // slot indices in launch order
+    std::vector<int> inflight;        // slots whose batch is on the GPU
+    std::deque<uint64_t> arena_order;  // batches holding arena space, in allocation order
+    std::vector<uint64_t> finished_seqs;  // batches done but whose space waits for an older one
+    uint64_t next_seq = 1;
     std::deque<u16wf::Request> completed;
     std::condition_variable cv_inflight;
     bool stopping = false;
@@ -284,24 +288,21 @@ static void launch_batch_slot(utf16_server *S, int si) {
     b.status = UTF16_OK;
     if (pos > b.unit_cap) {  // admission reserves an upper bound of this layout; never launch past it
         b.status = UTF16_ENOMEM;
-        cudaEventRecord(b.ev_done, S->s_d2h);
         return;
     }
 
     cudaError_t e = cudaMemcpyAsync(b.d_offsets, h_off, (size_t)(strings + 1) * sizeof(int64_t),
-                                    cudaMemcpyHostToDevice, S->s_h2d);
+                                    cudaMemcpyHostToDevice, b.stream);
     if (e == cudaSuccess && nd)
-        e = cudaMemcpyAsync(b.d_desc, h_desc, (size_t)nd * sizeof(CopyDesc), cudaMemcpyHostToDevice, S->s_h2d);
+        e = cudaMemcpyAsync(b.d_desc, h_desc, (size_t)nd * sizeof(CopyDesc), cudaMemcpyHostToDevice, b.stream);
     if (e == cudaSuccess && b.small_units)
-        e = cudaMemcpyAsync(b.d_units, h_units, (size_t)b.small_units * 2u, cudaMemcpyHostToDevice, S->s_h2d);
+        e = cudaMemcpyAsync(b.d_units, h_units, (size_t)b.small_units * 2u, cudaMemcpyHostToDevice, b.stream);
     for (const Request &r : b.reqs)
         if (e == cudaSuccess && r.large)
-            e = cudaMemcpyAsync(b.d_units + r.dev_off, r.in, (size_t)r.n * 2u, cudaMemcpyHostToDevice, S->s_h2d);
-    if (e == cudaSuccess) e = cudaEventRecord(b.ev_h2d, S->s_h2d);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_comp, b.ev_h2d, 0);
+            e = cudaMemcpyAsync(b.d_units + r.dev_off, r.in, (size_t)r.n * 2u, cudaMemcpyHostToDevice, b.stream);
     const int copy_blocks = std::max(1, std::min(S->ctx->sms * 8, (nd + 7) / 8));
     if (e == cudaSuccess && nd) {
-        copy_requests_kernel<true><<<copy_blocks, 256, 0, S->s_comp>>>(b.d_desc, nd, b.d_units);
+        copy_requests_kernel<true><<<copy_blocks, 256, 0, b.stream>>>(b.d_desc, nd, b.d_units);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -313,22 +314,20 @@ static void launch_batch_slot(utf16_server *S, int si) {
         L.first_bad = b.d_first;
         L.mode = kModeInPlaceFirst;
         configure_batch(S->ctx, S->ctx->batch_config(b.total_units, strings), L);
-        e = launch_batch(L, S->s_comp);
+        e = launch_batch(L, b.stream);
     }
     if (e == cudaSuccess && nd) {
-        copy_requests_kernel<false><<<copy_blocks, 256, 0, S->s_comp>>>(b.d_desc, nd, b.d_units);
+        copy_requests_kernel<false><<<copy_blocks, 256, 0, b.stream>>>(b.d_desc, nd, b.d_units);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaEventRecord(b.ev_kernel, S->s_comp);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_d2h, b.ev_kernel, 0);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h_first, b.d_first, (size_t)strings * sizeof(int64_t), cudaMemcpyDeviceToHost, S->s_d2h);
+        e = cudaMemcpyAsync(h_first, b.d_first, (size_t)strings * sizeof(int64_t), cudaMemcpyDeviceToHost, b.stream);
     if (e == cudaSuccess && b.small_units)
-        e = cudaMemcpyAsync(h_units, b.d_units, (size_t)b.small_units * 2u, cudaMemcpyDeviceToHost, S->s_d2h);
+        e = cudaMemcpyAsync(h_units, b.d_units, (size_t)b.small_units * 2u, cudaMemcpyDeviceToHost, b.stream);
     for (const Request &r : b.reqs)
         if (e == cudaSuccess && r.large)
-            e = cudaMemcpyAsync(r.out, b.d_units + r.dev_off, (size_t)r.n * 2u, cudaMemcpyDeviceToHost, S->s_d2h);
-    if (e == cudaSuccess) e = cudaEventRecord(b.ev_done, S->s_d2h);
+            e = cudaMemcpyAsync(r.out, b.d_units + r.dev_off, (size_t)r.n * 2u, cudaMemcpyDeviceToHost, b.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b.ev_done, b.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.status = UTF16_ECUDA;
@@ -404,6 +403,8 @@ static void scheduler_main(utf16_server *S) {
             continue;
         }
         S->free_slots.pop_front();
+        b.seq = S->next_seq++;
+        S->arena_order.push_back(b.seq);
         b.ring_off = ring_off;
         b.first_off = first_off;
         b.head_bytes = head;
@@ -432,20 +433,41 @@ static void scheduler_main(utf16_server *S) {
     S->cv_done.notify_all();
 }
 
+// Completes batches in the order they finish on the GPU (a batch of small
+// requests does not wait behind an older one that carries a large request),
+// and frees arena space in allocation order as the oldest batches finish.
 static void completer_main(utf16_server *S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
+    std::vector<int> polling;
     while (true) {
         S->cv_inflight.wait(lk, [&] { return !S->inflight.empty() || S->stopping; });
         if (S->inflight.empty() && S->stopping) break;
-        const int si = S->inflight.front();
-        BatchSlot &b = S->slots[(size_t)si];
+        polling = S->inflight;
         lk.unlock();
-        int status = b.status;
-        if (status == UTF16_OK && cudaEventSynchronize(b.ev_done) != cudaSuccess) {
-            cudaGetLastError();
-            status = UTF16_ECUDA;
+        int si = -1, status = UTF16_OK;
+        for (int cand : polling) {
+            const BatchSlot &c = S->slots[(size_t)cand];
+            if (c.status != UTF16_OK) {
+                si = cand;
+                status = c.status;
+                break;
+            }
+            const cudaError_t q = cudaEventQuery(c.ev_done);
+            if (q == cudaErrorNotReady) continue;
+            si = cand;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                status = UTF16_ECUDA;
+            }
+            break;
         }
+        if (si < 0) {
+            std::this_thread::yield();
+            lk.lock();
+            continue;
+        }
+        BatchSlot &b = S->slots[(size_t)si];
         const int64_t *h_first = (const int64_t *)(b.h_stage + b.first_off);
         const uint16_t *h_units = (const uint16_t *)(b.h_stage + b.head_bytes);
         for (int64_t s = 0; s < b.strings; ++s) {
@@ -466,8 +488,17 @@ static void completer_main(utf16_server *S) {
             S->stats.units += r.n;
         }
         b.reqs.clear();
-        S->ring->free_oldest();
-        S->inflight.pop_front();
+        S->inflight.erase(std::find(S->inflight.begin(), S->inflight.end(), si));
+        S->finished_seqs.push_back(b.seq);
+        for (bool freed = true; freed && !S->arena_order.empty();) {
+            auto it = std::find(S->finished_seqs.begin(), S->finished_seqs.end(), S->arena_order.front());
+            freed = it != S->finished_seqs.end();
+            if (freed) {
+                S->finished_seqs.erase(it);
+                S->arena_order.pop_front();
+                S->ring->free_oldest();
+            }
+        }
         S->free_slots.push_back(si);
         S->cv_sched.notify_all();
         S->cv_done.notify_all();
@@ -511,10 +542,6 @@ int utf16_server_create(const utf16_server_options *opt, utf16_server **out) {
         return UTF16_ENOMEM;
     }
     S->ring.reset(new FifoRing(o.hbm_budget_bytes));
-    if (cudaStreamCreateWithFlags(&S->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->s_d2h, cudaStreamNonBlocking) != cudaSuccess)
-        return UTF16_ECUDA;
     S->slots.resize((size_t)o.max_inflight_batches);
     for (int i = 0; i < o.max_inflight_batches; ++i) {
         BatchSlot &b = S->slots[(size_t)i];
@@ -523,8 +550,7 @@ int utf16_server_create(const utf16_server_options *opt, utf16_server **out) {
             cudaGetLastError();
             return UTF16_ENOMEM;
         }
-        if (cudaEventCreateWithFlags(&b.ev_h2d, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b.ev_kernel, cudaEventDisableTiming) != cudaSuccess ||
+        if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming) != cudaSuccess)
             return UTF16_ECUDA;
         S->free_slots.push_back(i);
@@ -644,19 +670,14 @@ int utf16_server_destroy(utf16_server *S) {
     }
     if (S->scheduler.joinable()) S->scheduler.join();
     if (S->completer.joinable()) S->completer.join();
-    cudaStreamSynchronize(S->s_h2d);
-    cudaStreamSynchronize(S->s_comp);
-    cudaStreamSynchronize(S->s_d2h);
+    for (BatchSlot &b : S->slots)
+        if (b.stream) cudaStreamSynchronize(b.stream);
     for (BatchSlot &b : S->slots) {
         if (b.h_stage) cudaFreeHost(b.h_stage);
-        if (b.ev_h2d) cudaEventDestroy(b.ev_h2d);
-        if (b.ev_kernel) cudaEventDestroy(b.ev_kernel);
         if (b.ev_done) cudaEventDestroy(b.ev_done);
+        if (b.stream) cudaStreamDestroy(b.stream);
     }
     if (S->arena) cudaFree(S->arena);
-    cudaStreamDestroy(S->s_h2d);
-    cudaStreamDestroy(S->s_comp);
-    cudaStreamDestroy(S->s_d2h);
     cudaGetLastError();
     delete S;
     return UTF16_OK;

@@ -301,3 +301,28 @@ def test_bench_launch_configuration_full_size(pkg):
         torch.cuda.empty_cache()
     finally:
         pkg.set_config(saved)
+
+
+def test_host_api_pinned_direct_and_mixed(pkg):
+    """Host-buffer API: both buffers pinned (one pass over the host link),
+    in place on a pinned buffer, misaligned pinned views, and a pinned input
+    with a pageable output (staged chunks) all give the oracle's result."""
+    import torch
+    rng = np.random.default_rng(83)
+    for n in (1, 7, 8, 3 * 4096 + 5, 1_000_003):
+        u = workloads.mixed(n, 1e-2, seed=int(rng.integers(1 << 30)))
+        want, want_fb = oracle.to_well_formed(u), oracle.first_bad(u)
+        for a in (0, 3):
+            base_in = torch.zeros(n + 8, dtype=torch.int16).pin_memory()
+            base_in[a:a + n] = torch.from_numpy(u.view(np.int16))
+            h_in = base_in[a:a + n]
+            h_out = torch.zeros(n + 8, dtype=torch.int16).pin_memory()[5 - a:5 - a + n]
+            out, fb = pkg.to_well_formed_host(h_in, h_out)
+            assert np.array_equal(out.numpy().view(np.uint16), want) and fb == want_fb, (n, a, "pinned")
+            assert np.all(base_in[:a].numpy() == 0) and np.all(base_in[a + n:].numpy() == 0)
+            out2, fb2 = pkg.to_well_formed_host(h_in, h_in)  # in place, pinned
+            assert np.array_equal(h_in.numpy().view(np.uint16), want) and fb2 == want_fb, (n, a, "in place")
+            h_in[:] = torch.from_numpy(u.view(np.int16))
+            pageable = np.zeros(n, np.uint16)
+            out3, fb3 = pkg.to_well_formed_host(h_in, pageable)
+            assert np.array_equal(pageable, want) and fb3 == want_fb, (n, a, "pinned in, pageable out")
