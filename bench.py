@@ -442,7 +442,7 @@ def e2e_measure(torch, wf, u, args):
     chunks = -(-u.size // chunk)
     return {"value": round(u.size * 2 / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(u.size * 2),
             "d2h_bytes_per_step": int(u.size * 2 + 8 * chunks), "ms_per_step": round(dt * 1e3, 3),
-            "api": "utf16_to_well_formed_host (pinned host buffers, 3-stream chunk pipeline)",
+            "api": "utf16_to_well_formed_host (pinned host buffers: one fused pass reading and writing host memory over the host link)",
             "first_bad": fbv}
 
 

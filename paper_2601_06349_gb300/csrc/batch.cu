@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
 
     const int lane = threadIdx.x & 31;
     WarpScratch<U> &ws = s_scratch[threadIdx.x >> 5];
+    enter_dependent_grid();
 
     const long long lo = A.offsets[0];
     const long long hi = A.offsets[A.count];
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
 
 // first_bad[s] = length of string s (the value for a well-formed string).
 __global__ void batch_lengths_kernel(const long long *offsets, long long count, long long *first_bad) {
+    enter_dependent_grid();
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
         first_bad[i] = offsets[i + 1] - offsets[i];
@@ -364,13 +366,17 @@ cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream) {
         long long blocks = (L.count + kBlockThreads - 1) / kBlockThreads;
         if (blocks > L.blocks) blocks = L.blocks;
         if (blocks < 1) blocks = 1;
-        batch_lengths_kernel<<<(unsigned)blocks, kBlockThreads, 0, stream>>>(L.offsets, L.count, L.first_bad);
-        cudaError_t e = cudaGetLastError();
+        const long long *offsets = L.offsets;
+        long long count = L.count;
+        long long *first_bad = L.first_bad;
+        void *largs[] = {(void *)&offsets, (void *)&count, (void *)&first_bad};
+        cudaError_t e = launch_kernel((const void *)batch_lengths_kernel, dim3((unsigned)blocks), dim3(kBlockThreads),
+                                      largs, 0, stream);
         if (e != cudaSuccess) return e;
     }
     const void *fn = pick_batch(L.mode, st, L.units_per_thread == 2 ? 2 : 4, L.prefetch);
     void *args[] = {(void *)&A};
-    return cudaLaunchKernel(fn, dim3((unsigned)L.blocks), dim3(kBlockThreads), args, 0, stream);
+    return launch_kernel(fn, dim3((unsigned)L.blocks), dim3(kBlockThreads), args, 0, stream);
 }
 
 const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch) {

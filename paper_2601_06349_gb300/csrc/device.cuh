@@ -247,6 +247,15 @@ __device__ __forceinline__ long long warp_min_ll(long long v) {
 }
 
 // 16-byte loads / stores.
+// Programmatic dependent launch: wait for the grids this one depends on (a
+// no-op when it was launched without the attribute), then let the next
+// launch on the stream start its blocks, which wait in turn.  Called first in
+// every kernel, before any global memory access.
+__device__ __forceinline__ void enter_dependent_grid() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint4 ld_stream(const uint4 *p) { return __ldcs(p); }
 __device__ __forceinline__ uint4 ld_plain(const uint4 *p) {
     uint4 v;

@@ -72,6 +72,11 @@ const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch = false);
 cudaError_t launch_check_offsets(const long long *offsets, long long count, Slot *slot, long long *result,
                                  int max_blocks, cudaStream_t stream);
 
+// Launch with programmatic dependent launch when enabled (the kernels start
+// with enter_dependent_grid()), else a plain launch.
+extern bool g_pdl;
+cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t stream);
+
 // Initialise a pool of scratch slots (min = all ones, done = 0).
 cudaError_t init_slots(Slot *slots, int count, cudaStream_t stream);
 

@@ -17,6 +17,7 @@ __global__ void __launch_bounds__(kBlockThreads) check_offsets_kernel(const long
                                                                       Slot *slot, long long *result) {
     __shared__ unsigned long long s_min;
     __shared__ bool s_last;
+    enter_dependent_grid();
     if (threadIdx.x == 0) s_min = ~0ull;
     __syncthreads();
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -53,8 +54,9 @@ cudaError_t launch_check_offsets(const long long *offsets, long long count, Slot
     long long blocks = (count + 1 + kBlockThreads - 1) / kBlockThreads;
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
-    check_offsets_kernel<<<(unsigned)blocks, kBlockThreads, 0, stream>>>(offsets, count, slot, result);
-    return cudaGetLastError();
+    void *args[] = {(void *)&offsets, (void *)&count, (void *)&slot, (void *)&result};
+    return launch_kernel((const void *)check_offsets_kernel, dim3((unsigned)blocks), dim3(kBlockThreads), args, 0,
+                         stream);
 }
 
 }  // namespace u16wf

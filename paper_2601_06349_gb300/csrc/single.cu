@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
     long long my_first = LLONG_MAX;
+    enter_dependent_grid();
 
     if constexpr (PF) {
         Chunk<U> nv;
@@ -144,7 +145,24 @@ cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream) {
     if (blocks > (long long)L.max_blocks) blocks = L.max_blocks;
     if (blocks < 1) blocks = 1;
     void *args[] = {(void *)&A};
-    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, 0, stream);
+    return launch_kernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, 0, stream);
+}
+
+bool g_pdl = false;
+
+cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t stream) {
+    if (!g_pdl) return cudaLaunchKernel(fn, grid, block, args, smem, stream);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 const void *single_kernel_for_occupancy(int mode, bool fb, int u, int variant) {

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
     const int warp = threadIdx.x >> 5;
     long long my_first = LLONG_MAX;
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
+    enter_dependent_grid();
 
     // Tiles of this block: tile_lo + blockIdx.x + k * gridDim.x.
     const long long first_tile = T.tile_lo + blockIdx.x;
@@ -268,7 +269,7 @@ cudaError_t launch_single_tma(const SingleLaunch &L, cudaStream_t stream) {
     long long blocks = work_blocks < (long long)L.max_blocks ? work_blocks : L.max_blocks;
     if (blocks < 1) blocks = 1;
     void *args[] = {(void *)&T};
-    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, kTmaSmemBytes, stream);
+    return launch_kernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, kTmaSmemBytes, stream);
 }
 
 cudaError_t prepare_single_tma() {
