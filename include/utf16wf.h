@@ -226,8 +226,9 @@ int utf16_set_config(const utf16_config *cfg);
 
 /*
  * Autotuner.  Times every candidate configuration (variant x units per thread
- * x blocks per SM) on the caller's own device buffers with CUDA events,
- * `reps` launches each after one warm-up, on a library stream; synchronous.
+ * x blocks per SM) on the caller's own device buffers with CUDA events, on a
+ * library stream: after one warm-up launch, three trials of `reps` launches
+ * each, the fastest trial counting; synchronous.
  * The fastest is stored for the size bucket floor(log2(n)) of single strings
  * (utf16_autotune_single: out-of-place repair with first-error index; then
  * the data path and grid of the read-only check, timed on the repaired

@@ -31,6 +31,23 @@ struct Timer {
     }
 };
 
+// Fastest of three trials of `reps` back-to-back launches (ms per trial):
+// the minimum keeps a candidate that met a slow moment from losing.
+template <typename F>
+bool time_trials(Timer &t, int reps, F launch, float *best) {
+    *best = 1e30f;
+    for (int trial = 0; trial < 3; ++trial) {
+        if (cudaEventRecord(t.a, t.s) != cudaSuccess) return false;
+        for (int r = 0; r < reps; ++r)
+            if (!launch()) return false;
+        if (cudaEventRecord(t.b, t.s) != cudaSuccess || cudaEventSynchronize(t.b) != cudaSuccess) return false;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) return false;
+        if (ms < *best) *best = ms;
+    }
+    return true;
+}
+
 // Blocks-per-SM candidates below the occupancy limit `fit` (0 = all that fit).
 std::vector<int> block_candidates(int fit) {
     std::vector<int> v = {0};
@@ -84,15 +101,11 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
                     cudaGetLastError();
                     return UTF16_ECUDA;
                 }
-                cudaEventRecord(t.a, t.s);
-                for (int r = 0; r < reps; ++r) launch_single(L, t.s);
-                cudaEventRecord(t.b, t.s);
-                if (cudaEventSynchronize(t.b) != cudaSuccess) {
+                float ms = 0.f;
+                if (!time_trials(t, reps, [&] { return launch_single(L, t.s) == cudaSuccess; }, &ms)) {
                     cudaGetLastError();
                     return UTF16_ECUDA;
                 }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, t.a, t.b);
                 if (ms < best_ms) {
                     best_ms = ms;
                     winner = c;
@@ -126,15 +139,11 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             cudaGetLastError();
             return UTF16_ECUDA;
         }
-        cudaEventRecord(t.a, t.s);
-        for (int r = 0; r < reps; ++r) launch_single(L, t.s);
-        cudaEventRecord(t.b, t.s);
-        if (cudaEventSynchronize(t.b) != cudaSuccess) {
+        float ms = 0.f;
+        if (!time_trials(t, reps, [&] { return launch_single(L, t.s) == cudaSuccess; }, &ms)) {
             cudaGetLastError();
             return UTF16_ECUDA;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, t.a, t.b);
         if (ms < best_check) {
             best_check = ms;
             check_winner = c;
@@ -147,14 +156,10 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
     {
         const size_t bytes = (size_t)n * 2u;
         auto timed = [&](const SingleLaunch *L, float *ms) -> bool {
-            cudaEventRecord(t.a, t.s);
-            for (int r = 0; r < reps; ++r) {
-                if (cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, t.s) != cudaSuccess) return false;
-                if (L && launch_single(*L, t.s) != cudaSuccess) return false;
-            }
-            cudaEventRecord(t.b, t.s);
-            if (cudaEventSynchronize(t.b) != cudaSuccess) return false;
-            return cudaEventElapsedTime(ms, t.a, t.b) == cudaSuccess;
+            return time_trials(t, reps, [&] {
+                return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, t.s) == cudaSuccess &&
+                       (!L || launch_single(*L, t.s) == cudaSuccess);
+            }, ms);
         };
         float copies = 0.f;
         if (!timed(nullptr, &copies)) {
@@ -231,15 +236,11 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
                     cudaGetLastError();
                     return UTF16_ECUDA;
                 }
-                cudaEventRecord(t.a, t.s);
-                for (int r = 0; r < reps; ++r) launch_batch(L, t.s);
-                cudaEventRecord(t.b, t.s);
-                if (cudaEventSynchronize(t.b) != cudaSuccess) {
+                float ms = 0.f;
+                if (!time_trials(t, reps, [&] { return launch_batch(L, t.s) == cudaSuccess; }, &ms)) {
                     cudaGetLastError();
                     return UTF16_ECUDA;
                 }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, t.a, t.b);
                 if (ms < best_ms) {
                     best_ms = ms;
                     winner = c;
