@@ -244,6 +244,21 @@ int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int64_t *offse
                          utf16_config *best);
 
 /*
+ * Autotuner without caller data, from a length histogram: the library makes
+ * synthetic mixed text (mostly ASCII and other BMP text, about 8 % of cells
+ * surrogate pairs and 1 % lone surrogates) and tunes on it.
+ *   op 0  single strings: length_histogram[b] > 0 tunes bucket b on one
+ *         string of 2^b units (at most 2^29; larger buckets take that result)
+ *   op 1  batches: length_histogram[b] strings with lengths in [2^b, 2^(b+1))
+ *         (bucket 0: 0 or 1 unit), shuffled into one batch of at most 2^29
+ *         units (counts scaled down in proportion), tuned for that batch's
+ *         string-count bucket and the histogram's own total
+ *   buckets  1..64 entries, none negative.
+ * Allocates and frees its own device buffers; synchronous.
+ */
+int utf16_autotune(int op, const int64_t *length_histogram, int buckets);
+
+/*
  * Tuned entries (what the autotuner stored), for saving and restoring a
  * tuning cache.  op: 0 = single strings (bucket = floor(log2(n))), 1 =
  * batches (bucket = floor(log2(num_strings))); bucket 0..63.

@@ -86,6 +86,7 @@ def _declare(lib):
         "utf16_autotune_single": ([vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_autotune_batch": ([vp, vp, vp, i64, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_check_device_errors": ([], ctypes.c_int),
+        "utf16_autotune": ([ctypes.c_int, vp, ctypes.c_int], ctypes.c_int),
         "utf16_get_tuned": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_set_tuned": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_error_positions": ([vp, i64, vp, i64, vp, vp], ctypes.c_int),
@@ -526,6 +527,16 @@ class Arena:
         if getattr(self, "_h", None):
             lib().utf16_arena_destroy(self._h)
             self._h = None
+
+
+def autotune_histogram(op: str, length_histogram) -> None:
+    """Tune from a histogram of lengths (bucket b = lengths in [2^b, 2^(b+1)))
+    on synthetic text: op "single" (one string per non-empty bucket) or
+    "batch" (one batch with the histogram's mix of string lengths)."""
+    import numpy as np
+    h = np.ascontiguousarray(np.asarray(length_histogram, dtype=np.int64))
+    code = {"single": 0, "batch": 1}[op]
+    _check(lib().utf16_autotune(code, h.ctypes.data, h.size), "utf16_autotune")
 
 
 def save_tuning(path: str) -> dict:

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/utf16wf.h"
@@ -256,4 +257,147 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
     }
     if (best) *best = winner;
     return UTF16_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tuning from a length histogram, on synthetic strings the library makes
+// itself: 16-bit hashes of the unit index give mostly ASCII and other BMP
+// text with about 8 % of its cells surrogate pairs and about 1 % lone
+// surrogates, so that the slow path runs as on mixed text.
+
+namespace u16wf {
+namespace {
+
+__device__ __forceinline__ uint32_t mix32(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xFF51AFD7ED558CCDull;
+    x ^= x >> 33;
+    x *= 0xC4CEB9FE1A85EC53ull;
+    x ^= x >> 33;
+    return (uint32_t)x;
+}
+
+// Cell k covers units 2k and 2k+1.
+__global__ void synth_text_kernel(uint16_t *u, long long n, uint64_t seed) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; 2 * k < n; k += stride) {
+        const uint32_t h = mix32(seed + (uint64_t)k);
+        const uint32_t kind = h % 100u;
+        uint16_t a, b;
+        if (kind < 8) {  // a pair
+            a = (uint16_t)(0xD800u + (h >> 8) % 1024u);
+            b = (uint16_t)(0xDC00u + (h >> 18) % 1024u);
+        } else if (kind < 9) {  // a lone surrogate, then ASCII
+            a = (uint16_t)(0xD800u + (h >> 8) % 2048u);
+            b = (uint16_t)(0x20u + (h >> 20) % 95u);
+        } else if (kind < 30) {  // BMP text outside the surrogates
+            a = (uint16_t)(0x0100u + (h >> 8) % 0xD700u);
+            b = (uint16_t)(0x0100u + (h >> 20) % 0xD700u);
+        } else {
+            a = (uint16_t)(0x20u + (h >> 8) % 95u);
+            b = (uint16_t)(0x20u + (h >> 16) % 95u);
+        }
+        u[2 * k] = a;
+        if (2 * k + 1 < n) u[2 * k + 1] = b;
+    }
+}
+
+constexpr long long kTuneMaxUnits = 1LL << 29;  // 1 GiB of synthetic input at most per tuning run
+
+}  // namespace
+}  // namespace u16wf
+
+extern "C" int utf16_autotune(int op, const int64_t *length_histogram, int buckets) {
+    if ((op != 0 && op != 1) || !length_histogram || buckets < 1 || buckets > 64) return UTF16_EINVAL;
+    for (int b = 0; b < buckets; ++b)
+        if (length_histogram[b] < 0) return UTF16_EINVAL;
+    DeviceCtx *ctx;
+    int rc = get_ctx(&ctx);
+    if (rc) return rc;
+    const int reps = 3;
+    if (op == 0) {
+        // every non-empty bucket b: one string of 2^b units (capped)
+        for (int b = 0; b < buckets; ++b) {
+            if (!length_histogram[b]) continue;
+            const long long n = std::min(1LL << b, kTuneMaxUnits);
+            uint16_t *in = nullptr, *out = nullptr;
+            if (cudaMalloc((void **)&in, (size_t)n * 2u) != cudaSuccess ||
+                cudaMalloc((void **)&out, (size_t)n * 2u) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(in);
+                return UTF16_ENOMEM;
+            }
+            synth_text_kernel<<<ctx->sms * 4, 256>>>(in, n, 0x2601063490ull + (uint64_t)b);
+            utf16_config cfg;
+            rc = cudaDeviceSynchronize() == cudaSuccess ? utf16_autotune_single(in, out, n, reps, &cfg) : UTF16_ECUDA;
+            cudaFree(in);
+            cudaFree(out);
+            cudaGetLastError();
+            if (rc) return rc;
+            if (bucket_of(n) != b) utf16_set_tuned(0, b, &cfg);  // sizes above the cap take the cap's result
+        }
+        return UTF16_OK;
+    }
+    // op 1: one batch whose string lengths follow the histogram (bucket b:
+    // lengths in [2^b, 2^(b+1)), bucket 0 also holds empty strings), scaled
+    // down to at most kTuneMaxUnits units in all
+    long long total_strings = 0;
+    double total_units = 0;
+    for (int b = 0; b < buckets; ++b) {
+        total_strings += length_histogram[b];
+        total_units += (double)length_histogram[b] * 1.5 * (double)(1LL << b);
+    }
+    if (total_strings == 0) return UTF16_OK;
+    const double scale = total_units > (double)kTuneMaxUnits ? (double)kTuneMaxUnits / total_units : 1.0;
+    std::vector<long long> lens;
+    uint64_t z = 0x9E3779B97F4A7C15ull;
+    for (int b = 0; b < buckets; ++b) {
+        const long long cnt = (long long)((double)length_histogram[b] * scale + 0.5);
+        for (long long i = 0; i < cnt; ++i) {
+            z ^= z << 13;
+            z ^= z >> 7;
+            z ^= z << 17;
+            lens.push_back(b == 0 ? (long long)(z % 2u) : (1LL << b) + (long long)(z % (uint64_t)(1LL << b)));
+        }
+    }
+    // interleave the buckets so that chunks see the mix
+    for (size_t i = lens.size(); i > 1; --i) {
+        z ^= z << 13;
+        z ^= z >> 7;
+        z ^= z << 17;
+        std::swap(lens[i - 1], lens[(size_t)(z % i)]);
+    }
+    const long long count = (long long)lens.size();
+    if (count == 0) return UTF16_OK;
+    long long units = 0;
+    for (long long v : lens) units += v;
+    if (units == 0) return UTF16_OK;
+    std::vector<int64_t> offs((size_t)count + 1, 0);
+    for (long long i = 0; i < count; ++i) offs[(size_t)i + 1] = offs[(size_t)i] + lens[(size_t)i];
+    uint16_t *in = nullptr, *out = nullptr;
+    int64_t *d_off = nullptr;
+    if (cudaMalloc((void **)&in, (size_t)units * 2u) != cudaSuccess ||
+        cudaMalloc((void **)&out, (size_t)units * 2u) != cudaSuccess ||
+        cudaMalloc((void **)&d_off, (size_t)(count + 1) * 8u) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(in);
+        cudaFree(out);
+        return UTF16_ENOMEM;
+    }
+    rc = UTF16_OK;
+    if (cudaMemcpy(d_off, offs.data(), (size_t)(count + 1) * 8u, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = UTF16_ECUDA;
+    if (!rc) {
+        synth_text_kernel<<<ctx->sms * 4, 256>>>(in, units, 0x2601063491ull);
+        if (cudaDeviceSynchronize() != cudaSuccess) rc = UTF16_ECUDA;
+    }
+    utf16_config cfg;
+    if (!rc) rc = utf16_autotune_batch(in, out, d_off, count, reps, &cfg);
+    cudaFree(in);
+    cudaFree(out);
+    cudaFree(d_off);
+    cudaGetLastError();
+    // a scaled-down batch also answers for the histogram's own string count
+    if (!rc && bucket_of(total_strings) != bucket_of(count)) utf16_set_tuned(1, bucket_of(total_strings), &cfg);
+    return rc;
 }

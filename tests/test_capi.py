@@ -75,6 +75,16 @@ def test_argument_errors_before_any_cuda_call(capi):
     assert capi.utf16_is_well_formed_batch(vp(4096), vp(64), 3, None, None) == -1
     # host entry point
     assert capi.utf16_to_well_formed_host(None, None, 3, None) == -1
+    # offsets check and histogram tuning
+    assert capi.utf16_check_offsets(None, 3, vp(4096), None) == -1
+    assert capi.utf16_check_offsets(vp(64), -1, vp(4096), None) == -1
+    hist = (ctypes.c_int64 * 4)(0, 1, 2, 3)
+    assert capi.utf16_autotune(2, hist, 4) == -1
+    assert capi.utf16_autotune(0, None, 4) == -1
+    assert capi.utf16_autotune(0, hist, 0) == -1
+    assert capi.utf16_autotune(1, hist, 65) == -1
+    bad = (ctypes.c_int64 * 2)(5, -1)
+    assert capi.utf16_autotune(1, bad, 2) == -1
 
 
 def test_empty_inputs_are_noops(capi):

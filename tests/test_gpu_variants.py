@@ -138,3 +138,45 @@ def test_tuning_cache_round_trip(pkg, tmp_path):
     c = pkg.Config()
     assert pkg.lib().utf16_get_tuned(0, u.size.bit_length() - 1, c) == 0
     assert c.as_dict() == cfg.as_dict()
+
+
+def test_autotune_from_length_histogram(pkg):
+    """utf16_autotune tunes size buckets (single strings) and a string-count
+    bucket (batches) on synthetic text; the tuned configurations then give
+    the oracle's results."""
+    import torch
+    saved = pkg.get_config()
+    try:
+        pkg.set_config(saved)  # clear tuned entries
+        hist = np.zeros(32, np.int64)
+        hist[12] = 5
+        hist[22] = 1
+        pkg.autotune_histogram("single", hist)
+        for b in (12, 22):
+            c = pkg.Config()
+            assert pkg.lib().utf16_get_tuned(0, b, c) == 0, b
+        assert pkg.lib().utf16_get_tuned(0, 13, pkg.Config()) == pkg.EAGAIN
+        bh = np.zeros(20, np.int64)
+        bh[0] = 50
+        bh[5] = 20_000
+        bh[11] = 300
+        pkg.autotune_histogram("batch", bh)
+        total = int(bh.sum())
+        assert pkg.lib().utf16_get_tuned(1, total.bit_length() - 1, pkg.Config()) == 0
+        # results under the tuned entries
+        u = workloads.mixed((1 << 22) + 5, 1e-2, seed=77)
+        d = to_dev(u)
+        out, fb = pkg.to_well_formed_first_bad(d)
+        assert np.array_equal(to_host(out), oracle.to_well_formed_threads(u))
+        assert int(fb.item()) == oracle.first_bad(u)
+        lens = workloads.lognormal_lengths(total, seed=78)
+        offs = workloads.offsets_from_lengths(lens)
+        units = workloads.mixed(int(offs[-1]), 1e-2, seed=79)
+        d_u = to_dev(units)
+        d_o = torch.from_numpy(offs).cuda()
+        got = to_host(pkg.to_well_formed_batch(d_u, d_o))
+        assert np.array_equal(got, oracle.to_well_formed_batch(units, offs))
+        fbb = pkg.first_error_index_batch(d_u, d_o).cpu().numpy()
+        assert np.array_equal(fbb, oracle.first_bad_batch(units, offs))
+    finally:
+        pkg.set_config(saved)
