@@ -178,7 +178,10 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
     }
 
     // String starts in [cfirst, cfirst + CU] as a byte map (0x80 per start).
+    // The barrier orders the previous chunk's reads of the scratch before
+    // these writes.
     constexpr int kStartVecs = (int)(CU + 16) / 16;
+    __syncwarp();
     for (int i = lane; i < kStartVecs; i += 32) reinterpret_cast<uint4 *>(ws.starts)[i] = make_uint4(0, 0, 0, 0);
     const long long cend = cfirst + CU;
     // One window of 32 offsets from the previous chunk's first string

@@ -68,7 +68,17 @@ int DeviceCtx::slot_for(cudaStream_t s, Slot **out) {
 utf16_config DeviceCtx::single_config(int64_t n) {
     std::lock_guard<std::mutex> lk(mu);
     const int b = bucket_of(n);
-    return single_has[b] ? single_tuned[b] : def;
+    if (single_has[b]) return single_tuned[b];
+    utf16_config c = def;
+    // The check's reduced default grid pays on long strings; on a string that
+    // gives each warp of it fewer than 8 chunks, the chunks' load latency
+    // dominates and all the blocks that fit finish sooner.
+    if (c.check_blocks_per_sm > 0) {
+        const int64_t chunk_units = (int64_t)c.single_units_per_thread * 256;
+        const int64_t warps = (int64_t)c.check_blocks_per_sm * sms * (kBlockThreads / 32);
+        if (n / chunk_units < 8 * warps) c.check_blocks_per_sm = 0;
+    }
+    return c;
 }
 
 utf16_config DeviceCtx::batch_config(int64_t units, int64_t count) {

@@ -37,7 +37,12 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
     long long my_first = LLONG_MAX;
+    __shared__ unsigned long long s_best;  // check: this block's smallest published mismatch
     enter_dependent_grid();
+    if constexpr (MODE == kModeCheck) {
+        if (threadIdx.x == 0) s_best = ~0ull;
+        __syncthreads();
+    }
 
     if constexpr (PF) {
         Chunk<U> nv;
@@ -58,7 +63,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
                 g = __shfl_sync(kFull, g, 0);
                 if (g != ~0ull && (long long)g < cfirst) break;
             }
-            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first);
+            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first, &s_best);
         }
     } else {
         for (long long c = gwarp; c < A.chunks; c += nwarps) {
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
                 g = __shfl_sync(kFull, g, 0);
                 if (g != ~0ull && (long long)g < cfirst) break;
             }
-            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first);
+            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first, &s_best);
         }
     }
 

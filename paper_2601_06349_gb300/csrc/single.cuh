@@ -102,7 +102,7 @@ __device__ __forceinline__ void store_chunk_vec(uint16_t *dst, int u, const uint
 // Steps 2-5 of the chunk starting at unit cfirst.
 template <int MODE, bool FB, int ST, int U>
 __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfirst, const Chunk<U> &ch, int lane,
-                                              long long &my_first) {
+                                              long long &my_first, unsigned long long *blk_best = nullptr) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     const bool edge = (cfirst < 0) || (cfirst + CU > A.n);
     const long long lfirst = cfirst + lane * kUnitsPerVec;  // this lane's first unit
@@ -197,10 +197,16 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
         }
     }
     if constexpr (FB && MODE == kModeCheck) {
-        // Publish early so that other warps can stop.
+        // Publish early so that other warps can stop: the block's best so far
+        // lives in shared memory (blk_best), and only a warp that improves
+        // on it updates the global minimum, so that strings with mismatches
+        // everywhere do not pile thousands of atomics onto one address.
         if (__any_sync(kFull, any_bad != 0)) {
             const long long wmin = warp_min_ll(my_first);
-            if (lane == 0) atomicMin(&A.slot->min, (unsigned long long)wmin);
+            if (lane == 0) {
+                const unsigned long long w = (unsigned long long)wmin;
+                if (atomicMin(blk_best, w) > w) atomicMin(&A.slot->min, w);
+            }
         }
     }
 }

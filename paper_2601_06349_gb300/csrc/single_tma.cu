@@ -125,7 +125,9 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
     const int warp = threadIdx.x >> 5;
     long long my_first = LLONG_MAX;
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
+    __shared__ unsigned long long s_best;  // check: this block's smallest published mismatch
     enter_dependent_grid();
+    if (threadIdx.x == 0) s_best = ~0ull;
 
     // Tiles of this block: tile_lo + blockIdx.x + k * gridDim.x.
     const long long first_tile = T.tile_lo + blockIdx.x;
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
             const long long c = e < n_lo ? e : T.edge_chunks_hi + (e - n_lo);
             Chunk<kTmaU> ch;
             load_chunk<MODE, kTmaU>(A, vin, c, lane, ch);
-            process_chunk<MODE, FB, 16, kTmaU>(A, c * (kTmaU * kWarpSliceUnits) - A.a, ch, lane, my_first);
+            process_chunk<MODE, FB, 16, kTmaU>(A, c * (kTmaU * kWarpSliceUnits) - A.a, ch, lane, my_first, &s_best);
         }
     }
 
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
             if (lane == 0) ch.halo = stage_units[r - 1];
             if (lane == 31) ch.halo = stage_units[r + kTmaU * kWarpSliceUnits];
             const long long cfirst = tile_first + (long long)warp * (kTmaU * kWarpSliceUnits);
-            process_chunk<MODE, FB, 16, kTmaU>(A, cfirst, ch, lane, my_first);
+            process_chunk<MODE, FB, 16, kTmaU>(A, cfirst, ch, lane, my_first, &s_best);
         }
         __syncthreads();  // every warp is done with stage s
         if (threadIdx.x == 0) {
