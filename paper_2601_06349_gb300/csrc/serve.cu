@@ -206,6 +206,89 @@ static void batch_head_layout(int64_t reqs, int64_t pieces, int64_t &first_off, 
 
 static int64_t pieces_of(const Request &r) { return r.direct ? (r.n + kPieceUnits - 1) / kPieceUnits : 0; }
 
+// Host copies between callers' buffers and a slot's pinned staging, spread
+// over a few worker threads (the calling thread works too).  Copies are cut
+// into pieces of at most 1 MiB so that the threads finish together; a list
+// of less than 256 KiB in all is copied by the caller alone.
+struct CopyJob {
+    void *dst;
+    const void *src;
+    size_t bytes;
+};
+
+class CopyPool {
+   public:
+    explicit CopyPool(int workers) {
+        for (int i = 0; i < workers; ++i) threads_.emplace_back([this] { loop(); });
+    }
+    ~CopyPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (std::thread &t : threads_) t.join();
+    }
+    void run(const std::vector<CopyJob> &jobs) {
+        size_t total = 0;
+        for (const CopyJob &j : jobs) total += j.bytes;
+        if (threads_.empty() || total < (256u << 10)) {
+            for (const CopyJob &j : jobs) memcpy(j.dst, j.src, j.bytes);
+            return;
+        }
+        std::unique_lock<std::mutex> lk(mu_);
+        // a worker that woke late for the previous list may still hold it
+        done_.wait(lk, [&] { return active_ == 0; });
+        pieces_.clear();
+        for (const CopyJob &j : jobs)
+            for (size_t o = 0; o < j.bytes; o += kPiece)
+                pieces_.push_back({(char *)j.dst + o, (const char *)j.src + o, std::min(kPiece, j.bytes - o)});
+        next_.store(0);
+        ++gen_;
+        const CopyJob *list = pieces_.data();
+        const size_t n = pieces_.size();
+        lk.unlock();
+        cv_.notify_all();
+        work(list, n);
+        lk.lock();
+        done_.wait(lk, [&] { return active_ == 0; });
+    }
+
+   private:
+    static constexpr size_t kPiece = 1u << 20;
+    void work(const CopyJob *list, size_t n) {
+        for (;;) {
+            const size_t i = next_.fetch_add(1);
+            if (i >= n) return;
+            memcpy(list[i].dst, list[i].src, list[i].bytes);
+        }
+    }
+    void loop() {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+            if (stop_) return;
+            seen = gen_;
+            ++active_;
+            const CopyJob *list = pieces_.data();
+            const size_t n = pieces_.size();
+            lk.unlock();
+            work(list, n);
+            lk.lock();
+            if (--active_ == 0) done_.notify_all();
+        }
+    }
+    std::vector<std::thread> threads_;
+    std::vector<CopyJob> pieces_;  // changed only while no worker is active
+    std::atomic<size_t> next_{0};
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    uint64_t gen_ = 0;
+    int active_ = 0;
+    bool stop_ = false;
+};
+
 }  // namespace u16wf
 
 struct utf16_server {
@@ -231,6 +314,7 @@ struct utf16_server {
     uint64_t next_ticket = 1;
     int64_t submitted = 0, finished = 0;
     utf16_server_stats stats;
+    std::unique_ptr<u16wf::CopyPool> pack_pool, unpack_pool;  // staging copies of the scheduler / completer
     std::thread scheduler, completer;
 };
 
@@ -262,11 +346,12 @@ static void launch_batch_slot(utf16_server *S, int si) {
     b.req_of_string.clear();
     b.small_units = 0;
     h_off[0] = 0;
+    std::vector<CopyJob> jobs;
     for (int i = 0; i < (int)b.reqs.size(); ++i) {
         Request &r = b.reqs[(size_t)i];
         const bool staged = !r.large && !r.direct;
         if (staged) {
-            memcpy(h_units + pos, r.in, (size_t)r.n * 2u);
+            jobs.push_back({h_units + pos, r.in, (size_t)r.n * 2u});
         } else if (pos % 8 != 0) {
             pos = align_up(pos, 8);
             h_off[++strings] = pos;  // padding string
@@ -282,6 +367,7 @@ static void launch_batch_slot(utf16_server *S, int si) {
         h_off[++strings] = pos;
         b.req_of_string.push_back(i);
     }
+    S->pack_pool->run(jobs);
     b.total_units = pos;
     b.strings = strings;
     b.ndirect = nd;
@@ -470,13 +556,15 @@ static void completer_main(utf16_server *S) {
         BatchSlot &b = S->slots[(size_t)si];
         const int64_t *h_first = (const int64_t *)(b.h_stage + b.first_off);
         const uint16_t *h_units = (const uint16_t *)(b.h_stage + b.head_bytes);
+        std::vector<CopyJob> jobs;
         for (int64_t s = 0; s < b.strings; ++s) {
             const int ri = b.req_of_string[(size_t)s];
             if (ri < 0) continue;
             Request &r = b.reqs[(size_t)ri];
-            if (status == UTF16_OK && !r.large && !r.direct) memcpy(r.out, h_units + r.dev_off, (size_t)r.n * 2u);
+            if (status == UTF16_OK && !r.large && !r.direct) jobs.push_back({r.out, h_units + r.dev_off, (size_t)r.n * 2u});
             r.first_bad = h_first[s];
         }
+        S->unpack_pool->run(jobs);
         const int64_t t_done = now_ns();
         lk.lock();
         for (Request &r : b.reqs) {
@@ -554,6 +642,12 @@ int utf16_server_create(const utf16_server_options *opt, utf16_server **out) {
             cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming) != cudaSuccess)
             return UTF16_ECUDA;
         S->free_slots.push_back(i);
+    }
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int workers = hw >= 16 ? 3 : hw >= 8 ? 1 : 0;
+        S->pack_pool.reset(new CopyPool(workers));
+        S->unpack_pool.reset(new CopyPool(workers));
     }
     utf16_server *raw = S.release();
     raw->scheduler = std::thread(scheduler_main, raw);
