@@ -216,6 +216,7 @@ typedef struct {
     int inplace_variant;         /* in-place repair of single strings: 0, 1 or 2 as single_variant */
     int check_blocks_per_sm;     /* read-only check: persistent grid = SMs x this; 0 = as many as fit */
     int inplace_blocks_per_sm;   /* in-place repair of single strings: the same */
+    int batch_check_prefetch;    /* per-string check of batches (utf16_is_well_formed_batch): 0 or 1 */
 } utf16_config;
 
 /* Default configuration of the current device (used where nothing is tuned). */

@@ -32,12 +32,38 @@ struct Timer {
     }
 };
 
+// Writes over twice the L2 before a trial, so that every candidate starts
+// with the same (cold) cache when the input does not fit in L2; otherwise the
+// first candidate after a pass that wrote the input's tail would start warm.
+struct L2Scrub {
+    void *buf = nullptr;
+    size_t bytes = 0;
+    L2Scrub(int64_t input_bytes) {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        if (input_bytes <= (int64_t)l2) return;
+        bytes = (size_t)l2 * 2;
+        if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            buf = nullptr;
+        }
+    }
+    ~L2Scrub() {
+        if (buf) cudaFree(buf);
+    }
+    bool run(cudaStream_t s) const { return !buf || cudaMemsetAsync(buf, 0, bytes, s) == cudaSuccess; }
+};
+
 // Fastest of three trials of `reps` back-to-back launches (ms per trial):
 // the minimum keeps a candidate that met a slow moment from losing.
 template <typename F>
-bool time_trials(Timer &t, int reps, F launch, float *best) {
+bool time_trials(Timer &t, int reps, F launch, float *best, const L2Scrub *scrub = nullptr) {
     *best = 1e30f;
     for (int trial = 0; trial < 3; ++trial) {
+        if (scrub && !scrub->run(t.s)) return false;
         if (cudaEventRecord(t.a, t.s) != cudaSuccess) return false;
         for (int r = 0; r < reps; ++r)
             if (!launch()) return false;
@@ -76,6 +102,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
     rc = ctx->slot_for(t.s, &slot);
     if (rc) return rc;
 
+    const L2Scrub scrub(n * 2);
     utf16_config base = ctx->def, winner = base;
     float best_ms = 1e30f;
     for (int variant = 0; variant <= 2; ++variant) {
@@ -103,7 +130,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
                     return UTF16_ECUDA;
                 }
                 float ms = 0.f;
-                if (!time_trials(t, reps, [&] { return launch_single(L, t.s) == cudaSuccess; }, &ms)) {
+                if (!time_trials(t, reps, [&] { return launch_single(L, t.s) == cudaSuccess; }, &ms, &scrub)) {
                     cudaGetLastError();
                     return UTF16_ECUDA;
                 }
@@ -141,7 +168,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             return UTF16_ECUDA;
         }
         float ms = 0.f;
-        if (!time_trials(t, reps, [&] { return launch_single(L, t.s) == cudaSuccess; }, &ms)) {
+        if (!time_trials(t, reps, [&] { return launch_single(L, t.s) == cudaSuccess; }, &ms, &scrub)) {
             cudaGetLastError();
             return UTF16_ECUDA;
         }
@@ -160,7 +187,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             return time_trials(t, reps, [&] {
                 return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, t.s) == cudaSuccess &&
                        (!L || launch_single(*L, t.s) == cudaSuccess);
-            }, ms);
+            }, ms, &scrub);
         };
         float copies = 0.f;
         if (!timed(nullptr, &copies)) {
@@ -215,6 +242,13 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
     if (rc) return rc;
     Timer t;
     if (!t.ok) return UTF16_ECUDA;
+    int64_t range[2] = {0, 0};  // offsets[0] and offsets[num_strings]: the batch's extent
+    if (cudaMemcpy(&range[0], offsets, 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&range[1], offsets + num_strings, 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    const L2Scrub scrub((range[1] - range[0]) * 2);
 
     utf16_config base = ctx->def, winner = base;
     float best_ms = 1e30f;
@@ -238,7 +272,7 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
                     return UTF16_ECUDA;
                 }
                 float ms = 0.f;
-                if (!time_trials(t, reps, [&] { return launch_batch(L, t.s) == cudaSuccess; }, &ms)) {
+                if (!time_trials(t, reps, [&] { return launch_batch(L, t.s) == cudaSuccess; }, &ms, &scrub)) {
                     cudaGetLastError();
                     return UTF16_ECUDA;
                 }
@@ -248,6 +282,43 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
                 }
             }
         }
+    }
+    // The per-string check: next chunk in flight or not, with the winner's
+    // other settings (its results go to a scratch array).
+    {
+        long long *scratch_fb = nullptr;
+        if (cudaMalloc((void **)&scratch_fb, (size_t)num_strings * 8u) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ENOMEM;
+        }
+        float best_check = 1e30f;
+        int best_pf = winner.batch_check_prefetch;
+        for (int pf = 0; pf <= 1; ++pf) {
+            utf16_config c = winner;
+            c.batch_check_prefetch = pf;
+            BatchLaunch L;
+            L.in = in;
+            L.offsets = (const long long *)offsets;
+            L.count = num_strings;
+            L.first_bad = scratch_fb;
+            L.mode = kModeCheck;
+            configure_batch(ctx, c, L);
+            float ms = 0.f;
+            if (launch_batch(L, t.s) != cudaSuccess ||
+                !time_trials(t, reps, [&] { return launch_batch(L, t.s) == cudaSuccess; }, &ms, &scrub)) {
+                cudaGetLastError();
+                cudaStreamSynchronize(t.s);
+                cudaFree(scratch_fb);
+                return UTF16_ECUDA;
+            }
+            if (ms < best_check) {
+                best_check = ms;
+                best_pf = pf;
+            }
+        }
+        cudaStreamSynchronize(t.s);
+        cudaFree(scratch_fb);
+        winner.batch_check_prefetch = best_pf;
     }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);

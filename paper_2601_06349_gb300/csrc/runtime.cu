@@ -92,6 +92,7 @@ static bool config_valid(const utf16_config &c) {
     return c.single_variant >= 0 && c.single_variant <= 2 && c.check_variant >= 0 && c.check_variant <= 2 &&
            c.inplace_variant >= 0 && c.inplace_variant <= 2 && c.check_blocks_per_sm >= 0 &&
            c.check_blocks_per_sm <= 64 && c.inplace_blocks_per_sm >= 0 && c.inplace_blocks_per_sm <= 64 &&
+           (c.batch_check_prefetch == 0 || c.batch_check_prefetch == 1) &&
            (c.inplace_unit_stores == 0 || c.inplace_unit_stores == 1) &&
            (c.single_units_per_thread == 2 || c.single_units_per_thread == 4) && c.single_blocks_per_sm >= 0 &&
            c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
@@ -150,12 +151,15 @@ int get_ctx(DeviceCtx **out) {
     // than all that fit (0.81 vs 0.75 of the copy peak, 1 GiB well-formed string).
     d.check_blocks_per_sm = env_int("UTF16WF_CHECK_BLOCKS_PER_SM", 3);
     d.inplace_blocks_per_sm = env_int("UTF16WF_INPLACE_BLOCKS_PER_SM", 0);
+    // The batch check runs faster without the next chunk in flight (77.5 vs
+    // 84-87 us on 1,000,000 strings), the batch repair faster with it (70 vs 75).
+    d.batch_check_prefetch = env_int("UTF16WF_BATCH_CHECK_PREFETCH", 0);
     // Programmatic dependent launch: back-to-back small calls measured 7-11 %
     // faster (1024 units 3.12 -> 2.89 us, 1,000,000 units 5.21 -> 4.68 us),
     // long ones unchanged.
     g_pdl = env_int("UTF16WF_PDL", 1) != 0;
     if (!config_valid(d))
-        d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg, 0, kVariantLdgPrefetch, 3, 0};
+        d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg, 0, kVariantLdgPrefetch, 3, 0, 0};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);
@@ -182,7 +186,7 @@ void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) 
 
 void configure_batch(DeviceCtx *ctx, const utf16_config &cfg, BatchLaunch &L) {
     L.units_per_thread = cfg.batch_units_per_thread;
-    L.prefetch = cfg.batch_prefetch != 0;
+    L.prefetch = (L.mode == kModeCheck ? cfg.batch_check_prefetch : cfg.batch_prefetch) != 0;
     const int fit = ctx->per_sm(batch_kernel_for_occupancy(L.mode, L.units_per_thread, L.prefetch), 0);
     const int per = cfg.batch_blocks_per_sm > 0 ? std::min(cfg.batch_blocks_per_sm, fit) : fit;
     L.blocks = per * ctx->sms;

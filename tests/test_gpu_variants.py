@@ -77,7 +77,7 @@ def test_single_configurations(pkg, strings, variant, u, bps):
 
 @pytest.mark.parametrize("u,pf,bps", BATCH)
 def test_batch_configurations(pkg, u, pf, bps):
-    pkg.set_config(batch_units_per_thread=u, batch_prefetch=pf, batch_blocks_per_sm=bps)
+    pkg.set_config(batch_units_per_thread=u, batch_prefetch=pf, batch_blocks_per_sm=bps, batch_check_prefetch=pf)
     from test_gpu_batch import _run_all_forms
     units, offs = workloads.ragged_batch(count=200_000, seed=77)
     _run_all_forms(pkg, units, offs, 0, 0, f"batch u={u} pf={pf}")
