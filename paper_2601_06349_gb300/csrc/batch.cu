@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
 
     const int lane = threadIdx.x & 31;
     WarpScratch<U> &ws = s_scratch[threadIdx.x >> 5];
-    enter_dependent_grid();
+    wait_prior_grids();
 
     const long long lo = A.offsets[0];
     const long long hi = A.offsets[A.count];
@@ -324,11 +324,12 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
             process_batch_chunk<MODE, ST, U>(A, vfirst * 8 - A.a, lo, hi, v, lane, ws, hint);
         }
     }
+    allow_next_grid();
 }
 
 // first_bad[s] = length of string s (the value for a well-formed string).
 __global__ void batch_lengths_kernel(const long long *offsets, long long count, long long *first_bad) {
-    enter_dependent_grid();
+    wait_prior_grids();
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
         first_bad[i] = offsets[i + 1] - offsets[i];

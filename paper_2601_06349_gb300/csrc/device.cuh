@@ -247,14 +247,16 @@ __device__ __forceinline__ long long warp_min_ll(long long v) {
 }
 
 // 16-byte loads / stores.
-// Programmatic dependent launch: wait for the grids this one depends on (a
-// no-op when it was launched without the attribute), then let the next
-// launch on the stream start its blocks, which wait in turn.  Called first in
-// every kernel, before any global memory access.
-__device__ __forceinline__ void enter_dependent_grid() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// Programmatic dependent launch.  wait_prior_grids(): wait for the grids this
+// one depends on (a no-op when it was launched without the attribute); called
+// first in every kernel, before any global memory access.
+// allow_next_grid(): this block's main work is done, the next launch on the
+// stream may start placing its blocks (which wait in turn).  Called after the
+// main loop, not at the start: blocks of the next launch that become resident
+// early sit in the SM slots a reduced persistent grid leaves free, and slowed
+// the read-only check (0.81 -> 0.56 of the peak at 3 blocks per SM).
+__device__ __forceinline__ void wait_prior_grids() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ uint4 ld_stream(const uint4 *p) { return __ldcs(p); }
 __device__ __forceinline__ uint4 ld_plain(const uint4 *p) {

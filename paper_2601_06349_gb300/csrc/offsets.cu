@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(kBlockThreads) check_offsets_kernel(const long
                                                                       Slot *slot, long long *result) {
     __shared__ unsigned long long s_min;
     __shared__ bool s_last;
-    enter_dependent_grid();
+    wait_prior_grids();
     if (threadIdx.x == 0) s_min = ~0ull;
     __syncthreads();
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kBlockThreads) check_offsets_kernel(const long
         }
     }
     if (mine != ~0ull) atomicMin(&s_min, mine);
+    allow_next_grid();
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_min != ~0ull) atomicMin(&slot->min, s_min);

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
     long long my_first = LLONG_MAX;
     __shared__ unsigned long long s_best;  // check: this block's smallest published mismatch
-    enter_dependent_grid();
+    wait_prior_grids();
     if constexpr (MODE == kModeCheck) {
         if (threadIdx.x == 0) s_best = ~0ull;
         __syncthreads();
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
         }
     }
 
+    allow_next_grid();
     if constexpr (FB) finish_first_bad(A, my_first, lane);
     if constexpr (MODE == kModeList) finish_list(A);
 }

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
     long long my_first = LLONG_MAX;
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
     __shared__ unsigned long long s_best;  // check: this block's smallest published mismatch
-    enter_dependent_grid();
+    wait_prior_grids();
     if (threadIdx.x == 0) s_best = ~0ull;
 
     // Tiles of this block: tile_lo + blockIdx.x + k * gridDim.x.
@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
         }
     }
     __syncthreads();
+    allow_next_grid();
     if constexpr (FB) finish_first_bad(A, my_first, lane);
 }
 
