@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip the variant / ragged / e2e measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="run the step in the library's default launch configuration instead of tuning first "
+                         "(for runs under a profiler, which distorts the tuner's timings)")
     ap.add_argument("--serve-requests", type=int, default=4000,
                     help="requests per arrival rate in the serving sweep")
     ap.add_argument("--ncu-case", choices=sorted(NCU_CASES), default=None,
@@ -357,7 +360,10 @@ def main():
     d_out = torch.empty_like(d_in)
     fb = torch.empty(1, dtype=torch.int64, device="cuda")
 
-    tuned = wf.autotune_single(d_in, d_out, reps=5)  # launch configuration for this size, as a user would
+    if args.no_autotune:
+        tuned = wf.get_config()
+    else:
+        tuned = wf.autotune_single(d_in, d_out, reps=5)  # launch configuration for this size, as a user would
     torch.cuda.synchronize()
 
     def step():
@@ -402,7 +408,8 @@ def main():
         "config": {"workload": WORKLOAD, "units": n, "l2": "inputs larger than L2 (1 GiB per step), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
-        "launch_config": {"autotuned": tuned.as_dict(), "block_threads": 256, "vector_bytes": 16},
+        "launch_config": {("default" if args.no_autotune else "autotuned"): tuned.as_dict(), "block_threads": 256,
+                          "vector_bytes": 16},
         "gpu_launches": args.steps,
         "clocks": clk,
     }

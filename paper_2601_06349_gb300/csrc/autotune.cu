@@ -4,6 +4,8 @@
 // kernels differ only in how data is brought in and how many blocks run).
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <vector>
@@ -56,6 +58,25 @@ struct L2Scrub {
     }
     bool run(cudaStream_t s) const { return !buf || cudaMemsetAsync(buf, 0, bytes, s) == cudaSuccess; }
 };
+
+// UTF16WF_TUNE_LOG=1 prints every candidate's time to stderr.
+bool tune_log() {
+    static const bool on = [] {
+        const char *e = getenv("UTF16WF_TUNE_LOG");
+        return e && *e && *e != '0';
+    }();
+    return on;
+}
+
+void log_candidate(const char *what, const utf16_config &c, float ms) {
+    if (!tune_log()) return;
+    fprintf(stderr,
+            "utf16wf tune %s: single v%d U%d bps%d | check v%d bps%d | inplace v%d bps%d | batch U%d pf%d bps%d "
+            "check-pf%d: %.4f ms\n",
+            what, c.single_variant, c.single_units_per_thread, c.single_blocks_per_sm, c.check_variant,
+            c.check_blocks_per_sm, c.inplace_variant, c.inplace_blocks_per_sm, c.batch_units_per_thread,
+            c.batch_prefetch, c.batch_blocks_per_sm, c.batch_check_prefetch, ms);
+}
 
 // Fastest of three trials of `reps` back-to-back launches (ms per trial):
 // the minimum keeps a candidate that met a slow moment from losing.
@@ -134,6 +155,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
                     cudaGetLastError();
                     return UTF16_ECUDA;
                 }
+                log_candidate("repair+first-error", c, ms);
                 if (ms < best_ms) {
                     best_ms = ms;
                     winner = c;
@@ -172,6 +194,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             cudaGetLastError();
             return UTF16_ECUDA;
         }
+        log_candidate("check", c, ms);
         if (ms < best_check) {
             best_check = ms;
             check_winner = c;
@@ -214,6 +237,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
                 cudaGetLastError();
                 return UTF16_ECUDA;
             }
+            log_candidate("in-place", c, ms - copies);
             if (ms - copies < best_inplace) {
                 best_inplace = ms - copies;
                 inplace_winner = c;
@@ -276,6 +300,7 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
                     cudaGetLastError();
                     return UTF16_ECUDA;
                 }
+                log_candidate("batch repair", c, ms);
                 if (ms < best_ms) {
                     best_ms = ms;
                     winner = c;
@@ -311,6 +336,7 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
                 cudaFree(scratch_fb);
                 return UTF16_ECUDA;
             }
+            log_candidate("batch check", c, ms);
             if (ms < best_check) {
                 best_check = ms;
                 best_pf = pf;
