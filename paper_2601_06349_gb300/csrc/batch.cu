@@ -380,7 +380,11 @@ cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream) {
     }
     const void *fn = pick_batch(L.mode, st, L.units_per_thread == 2 ? 2 : 4, L.prefetch);
     void *args[] = {(void *)&A};
-    return launch_kernel(fn, dim3((unsigned)L.blocks), dim3(kBlockThreads), args, 0, stream);
+    const long long warps = (long long)L.blocks * (kBlockThreads / 32);
+    const long long chunk_units = (L.units_per_thread == 2 ? 2 : 4) * (long long)kWarpSliceUnits;
+    const bool pdl = L.full_occupancy ||
+                     (L.units_hint > 0 && pdl_fits((L.units_hint / chunk_units + warps) / warps, false));
+    return launch_kernel(fn, dim3((unsigned)L.blocks), dim3(kBlockThreads), args, 0, stream, pdl);
 }
 
 const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch) {

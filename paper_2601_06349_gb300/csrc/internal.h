@@ -43,6 +43,7 @@ struct SingleLaunch {
     long long *positions = nullptr;  // kModeList: output array
     long long capacity = 0;          // kModeList: its length
     bool full_pass = false;          // kModeCheck: read the whole string (no early exit), for timing
+    bool full_occupancy = false;     // max_blocks is every block slot of the GPU
 };
 
 cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream);
@@ -62,6 +63,8 @@ struct BatchLaunch {
     int units_per_thread = 4;
     bool prefetch = false;
     int blocks = 1;                  // persistent grid size
+    bool full_occupancy = false;     // blocks is every block slot of the GPU
+    long long units_hint = 0;        // units in the batch when the caller knows them (0: unknown)
 };
 
 cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream);
@@ -72,10 +75,20 @@ const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch = false);
 cudaError_t launch_check_offsets(const long long *offsets, long long count, Slot *slot, long long *result,
                                  int max_blocks, cudaStream_t stream);
 
-// Launch with programmatic dependent launch when enabled (the kernels start
-// with enter_dependent_grid()), else a plain launch.
+// Launch with programmatic dependent launch when enabled and `pdl` allows it,
+// else a plain launch.  pdl_fits(): short launches (at most
+// kPdlMaxWorkPerWarp warp chunks per warp) are latency-bound and gain from
+// overlapping the next launch with this one's end; a grid with every block
+// slot of the GPU taken leaves the next launch no room to start early.  A
+// long launch on a reduced grid measured slower with it (the 1 GiB check at
+// 3 blocks per SM: 0.86 -> 0.79 of the copy peak back to back).
 extern bool g_pdl;
-cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t stream);
+constexpr long long kPdlMaxWorkPerWarp = 16;
+inline bool pdl_fits(long long work_per_warp, bool full_occupancy) {
+    return full_occupancy || work_per_warp <= kPdlMaxWorkPerWarp;
+}
+cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t stream,
+                          bool pdl = true);
 
 // Initialise a pool of scratch slots (min = all ones, done = 0).
 cudaError_t init_slots(Slot *slots, int count, cudaStream_t stream);

@@ -182,6 +182,7 @@ void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) 
                                               : cfg.single_blocks_per_sm;
     const int per = want > 0 ? std::min(want, fit) : fit;
     L.max_blocks = per * ctx->sms;
+    L.full_occupancy = per == fit;
 }
 
 void configure_batch(DeviceCtx *ctx, const utf16_config &cfg, BatchLaunch &L) {
@@ -190,6 +191,7 @@ void configure_batch(DeviceCtx *ctx, const utf16_config &cfg, BatchLaunch &L) {
     const int fit = ctx->per_sm(batch_kernel_for_occupancy(L.mode, L.units_per_thread, L.prefetch), 0);
     const int per = cfg.batch_blocks_per_sm > 0 ? std::min(cfg.batch_blocks_per_sm, fit) : fit;
     L.blocks = per * ctx->sms;
+    L.full_occupancy = per == fit;
 }
 
 static bool is_device_ptr(const void *p) {

@@ -400,6 +400,7 @@ static void launch_batch_slot(utf16_server *S, int si) {
         L.first_bad = b.d_first;
         L.mode = kModeInPlaceFirst;
         configure_batch(S->ctx, S->ctx->batch_config(b.total_units, strings), L);
+        L.units_hint = b.total_units;
         e = launch_batch(L, b.stream);
     }
     if (e == cudaSuccess && nd) {

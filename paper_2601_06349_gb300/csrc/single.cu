@@ -151,13 +151,16 @@ cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream) {
     if (blocks > (long long)L.max_blocks) blocks = L.max_blocks;
     if (blocks < 1) blocks = 1;
     void *args[] = {(void *)&A};
-    return launch_kernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, 0, stream);
+    const long long warps = blocks * warps_per_block;
+    return launch_kernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, 0, stream,
+                         pdl_fits((A.chunks + warps - 1) / warps, L.full_occupancy));
 }
 
 bool g_pdl = false;
 
-cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t stream) {
-    if (!g_pdl) return cudaLaunchKernel(fn, grid, block, args, smem, stream);
+cudaError_t launch_kernel(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t stream,
+                          bool pdl) {
+    if (!g_pdl || !pdl) return cudaLaunchKernel(fn, grid, block, args, smem, stream);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;

@@ -272,7 +272,9 @@ cudaError_t launch_single_tma(const SingleLaunch &L, cudaStream_t stream) {
     long long blocks = work_blocks < (long long)L.max_blocks ? work_blocks : L.max_blocks;
     if (blocks < 1) blocks = 1;
     void *args[] = {(void *)&T};
-    return launch_kernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, kTmaSmemBytes, stream);
+    const long long warps = blocks * (kBlockThreads / 32);
+    return launch_kernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, kTmaSmemBytes, stream,
+                         pdl_fits((T.s.chunks + warps - 1) / warps, L.full_occupancy));
 }
 
 cudaError_t prepare_single_tma() {
