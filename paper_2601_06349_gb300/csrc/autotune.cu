@@ -124,6 +124,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
     if (rc) return rc;
 
     const L2Scrub scrub(n * 2);
+    const PdlOffScope pdl_off;
     utf16_config base = ctx->def, winner = base;
     float best_ms = 1e30f;
     for (int variant = 0; variant <= 2; ++variant) {
@@ -273,6 +274,7 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
         return UTF16_ECUDA;
     }
     const L2Scrub scrub((range[1] - range[0]) * 2);
+    const PdlOffScope pdl_off;
 
     utf16_config base = ctx->def, winner = base;
     float best_ms = 1e30f;

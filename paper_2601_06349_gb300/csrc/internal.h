@@ -83,6 +83,13 @@ cudaError_t launch_check_offsets(const long long *offsets, long long count, Slot
 // long launch on a reduced grid measured slower with it (the 1 GiB check at
 // 3 blocks per SM: 0.86 -> 0.79 of the copy peak back to back).
 extern bool g_pdl;
+// Off for this thread while it lives (the autotuner compares kernels, not
+// overlaps between back-to-back launches).
+struct PdlOffScope {
+    PdlOffScope();
+    ~PdlOffScope();
+    bool saved;
+};
 constexpr long long kPdlMaxWorkPerWarp = 16;
 inline bool pdl_fits(long long work_per_warp, bool full_occupancy) {
     return full_occupancy || work_per_warp <= kPdlMaxWorkPerWarp;

@@ -68,17 +68,7 @@ int DeviceCtx::slot_for(cudaStream_t s, Slot **out) {
 utf16_config DeviceCtx::single_config(int64_t n) {
     std::lock_guard<std::mutex> lk(mu);
     const int b = bucket_of(n);
-    if (single_has[b]) return single_tuned[b];
-    utf16_config c = def;
-    // The check's reduced default grid pays on long strings; on a string that
-    // gives each warp of it fewer than 8 chunks, the chunks' load latency
-    // dominates and all the blocks that fit finish sooner.
-    if (c.check_blocks_per_sm > 0) {
-        const int64_t chunk_units = (int64_t)c.single_units_per_thread * 256;
-        const int64_t warps = (int64_t)c.check_blocks_per_sm * sms * (kBlockThreads / 32);
-        if (n / chunk_units < 8 * warps) c.check_blocks_per_sm = 0;
-    }
-    return c;
+    return single_has[b] ? single_tuned[b] : def;
 }
 
 utf16_config DeviceCtx::batch_config(int64_t units, int64_t count) {
@@ -147,9 +137,7 @@ int get_ctx(DeviceCtx **out) {
     // 0.68 of the copy peak); out of place with the first-error index the
     // plain loads are (0.93 vs 0.89).
     d.inplace_variant = env_int("UTF16WF_INPLACE_VARIANT", kVariantLdgPrefetch);
-    // The read-only check streams best with 3 resident blocks per SM rather
-    // than all that fit (0.81 vs 0.75 of the copy peak, 1 GiB well-formed string).
-    d.check_blocks_per_sm = env_int("UTF16WF_CHECK_BLOCKS_PER_SM", 3);
+    d.check_blocks_per_sm = env_int("UTF16WF_CHECK_BLOCKS_PER_SM", 0);
     d.inplace_blocks_per_sm = env_int("UTF16WF_INPLACE_BLOCKS_PER_SM", 0);
     // The batch check runs faster without the next chunk in flight (77.5 vs
     // 84-87 us on 1,000,000 strings), the batch repair faster with it (70 vs 75).
@@ -159,7 +147,7 @@ int get_ctx(DeviceCtx **out) {
     // long ones unchanged.
     g_pdl = env_int("UTF16WF_PDL", 1) != 0;
     if (!config_valid(d))
-        d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg, 0, kVariantLdgPrefetch, 3, 0, 0};
+        d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg, 0, kVariantLdgPrefetch, 0, 0, 0};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);

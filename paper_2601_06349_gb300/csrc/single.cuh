@@ -198,9 +198,11 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
     }
     if constexpr (FB && MODE == kModeCheck) {
         // Publish early so that other warps can stop: the block's best so far
-        // lives in shared memory (blk_best), and only a warp that improves
-        // on it updates the global minimum, so that strings with mismatches
-        // everywhere do not pile thousands of atomics onto one address.
+        // lives in shared memory (blk_best, which also takes in the global
+        // minimum when a warp of the block polls it), and only a warp that
+        // improves on it updates the global minimum, so that strings with
+        // mismatches everywhere do not pile thousands of atomics onto one
+        // address.
         if (__any_sync(kFull, any_bad != 0)) {
             const long long wmin = warp_min_ll(my_first);
             if (lane == 0) {
