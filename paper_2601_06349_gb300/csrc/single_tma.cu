@@ -188,8 +188,8 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
         const uint16_t *stage_units = reinterpret_cast<const uint16_t *>(stage);
         bool skip = false;
         if constexpr (MODE == kModeCheck) {
-            if (!A.full_pass) {
-                const unsigned long long g = *((volatile unsigned long long *)&A.slot->min);
+            if (!A.full_pass) {  // the block's shared best: thread 0 folds the global minimum into it
+                const unsigned long long g = *((volatile unsigned long long *)&s_best);
                 skip = (g != ~0ull && (long long)g < tile_first);
             }
         }
@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_tma_kernel(const TmaArgs
             bool go = next < my_tiles;
             if constexpr (MODE == kModeCheck) {
                 const unsigned long long g = *((volatile unsigned long long *)&A.slot->min);
+                if (g != ~0ull) atomicMin(&s_best, g);
                 if (!A.full_pass && g != ~0ull && (long long)g < (first_tile + next * gridDim.x) * kTileUnits - A.a)
                     go = false;
             }
