@@ -130,7 +130,8 @@ int utf16_error_positions(const uint16_t *in, int64_t n, int64_t *positions, int
  *              (it need not be 0).  The library reads the range from the
  *              device, so a call never synchronises with the host.  Offsets
  *              that decrease give unspecified (but memory-safe within
- *              [offsets[0], offsets[num_strings]) output.
+ *              [offsets[0], offsets[num_strings]) output, unless checked
+ *              mode (utf16_set_checked) rejects them first.
  *   in, out    device buffers indexed by the offsets; only units in
  *              [offsets[0], offsets[num_strings]) are read or written.
  * Each string is repaired on its own: its first unit has no left neighbour
@@ -159,6 +160,18 @@ int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64
  */
 int utf16_check_offsets(const int64_t *offsets, int64_t num_strings, int64_t *first_violation,
                         utf16_stream_t stream);
+
+/*
+ * Checked mode (process-wide; initially the value of the environment
+ * variable UTF16WF_CHECKED, off when unset or 0).  When on, the three batch
+ * entry points above run the utf16_check_offsets pass first and wait for it:
+ * invalid offsets return UTF16_EINVAL with nothing launched.  The calls then
+ * synchronise with the host, so inside a CUDA stream capture they return
+ * UTF16_EINVAL.  The serving engine builds its own offsets and is not
+ * affected.  utf16_set_checked returns UTF16_OK; utf16_get_checked 1 or 0.
+ */
+int utf16_set_checked(int on);
+int utf16_get_checked(void);
 
 /*
  * toWellFormed plus first-error index on HOST buffers.  Blocking: returns

@@ -91,6 +91,8 @@ def _declare(lib):
         "utf16_set_tuned": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(Config)], ctypes.c_int),
         "utf16_error_positions": ([vp, i64, vp, i64, vp, vp], ctypes.c_int),
         "utf16_check_offsets": ([vp, i64, vp, vp], ctypes.c_int),
+        "utf16_set_checked": ([ctypes.c_int], ctypes.c_int),
+        "utf16_get_checked": ([], ctypes.c_int),
         "utf16_selftest_bounded_wait": ([i64], ctypes.c_int),
         "utf16_to_well_formed_first_bad_noalloc": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "utf16_release_device": ([], ctypes.c_int),
@@ -307,6 +309,16 @@ def check_offsets(offsets, *, stream=None) -> int:
         _check(lib().utf16_check_offsets(offsets.data_ptr(), offsets.numel() - 1, ctypes.byref(out),
                                          _stream(stream, offsets.device)), "utf16_check_offsets")
     return out.value
+
+
+def set_checked(on: bool) -> None:
+    """Checked mode: the batch calls validate their offsets first (one pass
+    and a wait for the stream) and raise on invalid offsets."""
+    _check(lib().utf16_set_checked(1 if on else 0), "utf16_set_checked")
+
+
+def get_checked() -> bool:
+    return lib().utf16_get_checked() != 0
 
 
 def to_well_formed_host(host_in, host_out=None):

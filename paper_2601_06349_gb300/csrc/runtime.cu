@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <memory>
 #include <mutex>
 #include <unordered_map>
@@ -249,11 +250,52 @@ static int empty_first_bad(int64_t *first_bad, cudaStream_t stream) {
     return UTF16_OK;
 }
 
+// Checked mode: -1 until first read (then UTF16WF_CHECKED, default off).
+static std::atomic<int> g_checked{-1};
+
+static bool checked_mode() {
+    int c = g_checked.load(std::memory_order_relaxed);
+    if (c < 0) {
+        int expected = -1;
+        g_checked.compare_exchange_strong(expected, env_int("UTF16WF_CHECKED", 0) != 0 ? 1 : 0);
+        c = g_checked.load(std::memory_order_relaxed);
+    }
+    return c != 0;
+}
+
+// The offsets check of utf16_check_offsets into the stream's slot, read back
+// on the host: *violation = smallest violating index or -1.
+static int validate_offsets(DeviceCtx *ctx, const int64_t *offsets, int64_t count, cudaStream_t s,
+                            int64_t *violation) {
+    Slot *slot = nullptr;
+    int rc = ctx->slot_for(s, &slot);
+    if (rc) return rc;
+    if (launch_check_offsets((const long long *)offsets, count, slot, &slot->result, ctx->sms * 8, s) != cudaSuccess ||
+        cudaMemcpyAsync(violation, &slot->result, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return UTF16_ECUDA;
+    }
+    return UTF16_OK;
+}
+
 int run_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t count, int mode, int64_t *first_bad,
               cudaStream_t stream) {
     DeviceCtx *ctx;
     int rc = get_ctx(&ctx);
     if (rc) return rc;
+    if (checked_mode()) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+        if (cap != cudaStreamCaptureStatusNone) return UTF16_EINVAL;  // the check must read back
+        int64_t violation = -1;
+        rc = validate_offsets(ctx, offsets, count, stream, &violation);
+        if (rc) return rc;
+        if (violation >= 0) return UTF16_EINVAL;
+    }
     BatchLaunch L;
     L.in = in;
     L.out = out;
@@ -493,6 +535,13 @@ int utf16_is_well_formed_batch(const uint16_t *in, const int64_t *offsets, int64
         return UTF16_EINVAL;
     return run_batch(in, nullptr, offsets, num_strings, kModeCheck, first_bad, (cudaStream_t)stream);
 }
+
+int utf16_set_checked(int on) {
+    g_checked.store(on != 0 ? 1 : 0, std::memory_order_relaxed);
+    return UTF16_OK;
+}
+
+int utf16_get_checked(void) { return checked_mode() ? 1 : 0; }
 
 int utf16_check_offsets(const int64_t *offsets, int64_t num_strings, int64_t *first_violation,
                         utf16_stream_t stream) {

@@ -105,3 +105,26 @@ def test_binding_rejects_cpu_tensors(capi):
         pkg.to_well_formed(torch.zeros(4, dtype=torch.int16))
     with pytest.raises(TypeError):
         pkg.to_well_formed(torch.zeros(4, dtype=torch.float32))
+
+
+def test_checked_mode_switch(capi):
+    """utf16_set_checked / utf16_get_checked need no GPU; the initial value
+    comes from UTF16WF_CHECKED."""
+    import subprocess
+    import sys
+    import paper_2601_06349_gb300 as pkg
+    was = pkg.get_checked()
+    try:
+        pkg.set_checked(True)
+        assert capi.utf16_get_checked() == 1
+        pkg.set_checked(False)
+        assert not pkg.get_checked()
+    finally:
+        pkg.set_checked(was)
+    code = "import paper_2601_06349_gb300 as p; print(p.get_checked())"
+    for env_value, want in (("1", "True"), ("0", "False"), ("", "False")):
+        env = dict(os.environ, UTF16WF_CHECKED=env_value)
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=120)
+        assert out.returncode == 0, out.stderr
+        assert out.stdout.strip() == want, (env_value, out.stdout)

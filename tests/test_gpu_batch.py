@@ -3,6 +3,8 @@ the C ABI: every string of length <= 5 over the border alphabet as one batch
 (at several base misalignments and a nonzero first offset), the 1,000,000
 string log-normal batch, and degenerate batches (all empty, one string, runs
 of empty strings, strings longer than a chunk)."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -146,3 +148,53 @@ def test_check_offsets(pkg):
     out = pkg.to_well_formed_batch(torch.from_numpy(units.view(np.int16)).cuda(), d)
     lo, hi = int(good[0]), int(good[-1])
     assert np.array_equal(out.cpu().numpy().view(np.uint16)[lo:hi], oracle.to_well_formed_batch(units, good)[lo:hi])
+
+
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")  # the refused call captures nothing
+def test_checked_mode(pkg):
+    """In checked mode every batch entry point rejects invalid offsets with
+    UTF16_EINVAL before launching (buffers untouched), accepts valid ones,
+    and refuses to run inside a stream capture."""
+    import torch
+    lens = workloads.lognormal_lengths(50_000, seed=73)
+    good = workloads.offsets_from_lengths(lens.astype(np.int64), start=2)
+    units = workloads.mixed(int(good[-1]) + 8, 1e-2, seed=74)
+    want = oracle.to_well_formed_batch(units, good)
+    want_fb = oracle.first_bad_batch(units, good)
+    bad = good.copy()
+    bad[1234] = bad[1233] - 1
+    d_u = torch.from_numpy(units.view(np.int16)).cuda()
+    d_good = torch.from_numpy(good).cuda()
+    d_bad = torch.from_numpy(bad).cuda()
+    was = pkg.get_checked()
+    pkg.set_checked(True)
+    try:
+        out = torch.full_like(d_u, 0x1234)
+        fb = torch.full((good.size - 1,), -5, dtype=torch.int64, device="cuda")
+        buf = d_u.clone()
+        for call in (lambda: pkg.to_well_formed_batch(d_u, d_bad, out),
+                     lambda: pkg.to_well_formed_batch_(buf, d_bad),
+                     lambda: pkg.first_error_index_batch(d_u, d_bad, fb)):
+            with pytest.raises(pkg.Utf16Error) as e:
+                call()
+            assert e.value.code == pkg.EINVAL
+        torch.cuda.synchronize()
+        assert bool((out == 0x1234).all()) and bool((fb == -5).all()) and torch.equal(buf, d_u)
+        lo, hi = int(good[0]), int(good[-1])
+        pkg.to_well_formed_batch(d_u, d_good, out)
+        assert np.array_equal(out.cpu().numpy().view(np.uint16)[lo:hi], want[lo:hi])
+        pkg.first_error_index_batch(d_u, d_good, fb)
+        assert np.array_equal(fb.cpu().numpy(), want_fb)
+        pkg.to_well_formed_batch_(buf, d_good)
+        assert np.array_equal(buf.cpu().numpy().view(np.uint16)[lo:hi], want[lo:hi])
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.graph(g, stream=s):
+                rc = pkg.lib().utf16_to_well_formed_batch(d_u.data_ptr(), out.data_ptr(), d_good.data_ptr(),
+                                                          good.size - 1, ctypes.c_void_p(s.cuda_stream))
+        assert rc == pkg.EINVAL
+    finally:
+        pkg.set_checked(was)
+    pkg.check_device_errors()

@@ -85,6 +85,30 @@ def test_batch_configurations(pkg, u, pf, bps):
     pkg.check_device_errors()
 
 
+@pytest.mark.parametrize("u,pf,bps", BATCH)
+def test_batch_split_pairs_at_every_start_position(pkg, u, pf, bps):
+    """Pairs cut by string starts at every position of a chunk, its slices
+    and vectors: a text of high-low pairs (a few units replaced by ASCII or
+    lone surrogates) split into strings of 0-4 units, then into a mix with
+    strings longer than a chunk.  A start at an odd position splits a pair."""
+    pkg.set_config(batch_units_per_thread=u, batch_prefetch=pf, batch_blocks_per_sm=bps, batch_check_prefetch=pf)
+    from test_gpu_batch import _run_all_forms
+    rng = np.random.default_rng(1000 + 10 * u + pf)
+    n = 300_000
+    units = np.tile(np.array([0xD800, 0xDC00], np.uint16), n // 2)
+    noise = rng.random(n) < 0.02
+    units[noise] = rng.choice(np.array([0x41, 0xD800, 0xDBFF, 0xDC00, 0xDFFF], np.uint16), int(noise.sum()))
+    short = rng.integers(0, 5, n)
+    mixed = np.where(rng.random(n) < 0.3, rng.integers(200, 1500, n), rng.integers(0, 5, n))
+    for label, lens in (("short", short), ("mixed", mixed)):
+        total = np.cumsum(lens)
+        lens = lens[: int(np.searchsorted(total, n - 8))]
+        offs = workloads.offsets_from_lengths(lens.astype(np.int64), start=1)
+        for a_in, a_out in ((0, 0), (3, 5), (7, 1)):
+            _run_all_forms(pkg, units, offs, a_in, a_out, f"split pairs {label} u={u} pf={pf}")
+    pkg.check_device_errors()
+
+
 def test_autotuner_choice_is_correct(pkg):
     import torch
     u = workloads.mixed(64 << 20, 1e-2, seed=51)
