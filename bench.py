@@ -65,25 +65,25 @@ def parse():
     return ap.parse_args()
 
 
-NCU_CASES = {"single_out_fb", "single_out", "single_check", "single_inplace", "batch_out", "batch_check",
-             "batch_inplace"}
+NCU_CASES = {"single_out_fb", "single_out_fb_clean", "single_out", "single_check", "single_inplace", "batch_out",
+             "batch_check", "batch_inplace"}
 
 
 def run_ncu_case(name):
     """Six launches of one kernel on a case small enough for a full ncu
-    capture (256 MiB mixed string at 1e-2 lone rate, or the 1,000,000-string
-    ragged batch).  The launch configuration is the library default (override
+    capture (256 MiB mixed string at 1e-2 lone rate, without lone surrogates
+    for the check and `_clean`, or the 1,000,000-string ragged batch).  The launch configuration is the library default (override
     with the UTF16WF_* environment variables)."""
     import torch
     import paper_2601_06349_gb300 as wf
     wf.init_device()
     if name.startswith("single"):
-        u = workloads.mixed(1 << 27, 1e-2 if name != "single_check" else 0.0, seed=99)
+        u = workloads.mixed(1 << 27, 0.0 if name in ("single_check", "single_out_fb_clean") else 1e-2, seed=99)
         d = torch.from_numpy(u.view(np.int16)).cuda()
         o = torch.empty_like(d)
         fb = torch.empty(1, dtype=torch.int64, device="cuda")
         for _ in range(6):
-            if name == "single_out_fb":
+            if name in ("single_out_fb", "single_out_fb_clean"):
                 wf.to_well_formed_first_bad(d, o, fb)
             elif name == "single_out":
                 wf.to_well_formed(d, o)
@@ -255,10 +255,14 @@ def graph_calls_ms(torch, fn, stream, calls=64, replays=8, fn_makes_all=False):
     return time_launches(torch, g.replay, replays, stream) / (replays * calls)
 
 
-def time_launches(torch, fn, steps, stream):
-    """CUDA-event time (ms) of `steps` back-to-back calls on `stream`."""
+def time_launches(torch, fn, steps, stream, warmup=0):
+    """CUDA-event time (ms) of `steps` back-to-back calls on `stream`, after
+    `warmup` untimed calls (the first call on freshly allocated memory pays for
+    its first touch: 681 vs 370 us on a new 1 GiB string)."""
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        fn()
     torch.cuda.synchronize()
     start.record(stream)
     for _ in range(steps):
@@ -509,15 +513,16 @@ def variants(torch, wf, stream, d_in, d_out, u_main):
             src = pristine
         else:
             src = torch.from_numpy(workloads.large_mixed(rate).view(np.int16)).cuda()
-        ms = time_launches(torch, lambda: wf.to_well_formed_first_bad(src, d_out, stream=stream), steps, stream) / steps
+        ms = time_launches(torch, lambda: wf.to_well_formed_first_bad(src, d_out, stream=stream), steps, stream,
+                           warmup=3) / steps
         rec(f"1GiB_p{rate:g}_out_first_bad", n, ms, 4)
-        ms = time_launches(torch, lambda: wf.to_well_formed(src, d_out, stream=stream), steps, stream) / steps
+        ms = time_launches(torch, lambda: wf.to_well_formed(src, d_out, stream=stream), steps, stream, warmup=3) / steps
         rec(f"1GiB_p{rate:g}_out", n, ms, 4)
         ch = changed_units(src, d_out)
         ms = timed_inplace(d_in, src, 3)
         rec(f"1GiB_p{rate:g}_inplace", n, ms, 2 + 2 * ch / n)
         res[f"1GiB_p{rate:g}_inplace"]["changed_units"] = ch
-        ms = time_launches(torch, lambda: wf.first_error_index(src, stream=stream), steps, stream) / steps
+        ms = time_launches(torch, lambda: wf.first_error_index(src, stream=stream), steps, stream, warmup=3) / steps
         rec(f"1GiB_p{rate:g}_is_well_formed", n, ms, 2)
         if ch:
             res[f"1GiB_p{rate:g}_is_well_formed"]["note"] = "stops early at the first error"
@@ -529,7 +534,7 @@ def variants(torch, wf, stream, d_in, d_out, u_main):
     a_buf = d_in[:na]
     for kind in ("uniform", "shifted", "all_high"):
         src = torch.from_numpy(workloads.adversarial(kind).view(np.int16)).cuda()
-        ms = time_launches(torch, lambda: wf.to_well_formed(src, a_out, stream=stream), steps, stream) / steps
+        ms = time_launches(torch, lambda: wf.to_well_formed(src, a_out, stream=stream), steps, stream, warmup=3) / steps
         rec(f"512MiB_{kind}_out", na, ms, 4)
         ch = changed_units(src, a_out)
         ms = timed_inplace(a_buf, src, 3)
@@ -541,7 +546,7 @@ def variants(torch, wf, stream, d_in, d_out, u_main):
     s_out = torch.empty_like(small)
     s_fb = torch.empty(1, dtype=torch.int64, device="cuda")
     ms = time_launches(torch, lambda: wf.to_well_formed_first_bad(small, s_out, s_fb, stream=stream), 200,
-                       stream) / 200
+                       stream, warmup=3) / 200
     rec("1MiB_mixed_out_first_bad_L2_resident", small.numel(), ms, 4)
     g = capture_graph(torch, lambda: wf.to_well_formed_first_bad(small, s_out, s_fb))
     ms = time_launches(torch, g.replay, 200, stream) / 200
