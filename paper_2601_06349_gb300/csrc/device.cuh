@@ -246,6 +246,23 @@ __device__ __forceinline__ long long warp_min_ll(long long v) {
     return v;
 }
 
+// Completion counters of the last-block pattern.  The add has acquire and
+// release semantics at GPU scope: it orders this thread's earlier writes (its
+// block's atomicMin) before the count, and the block that brings the count to
+// the grid size sees every other block's earlier writes, with no separate
+// fence on either side.
+__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // 16-byte loads / stores.
 // Programmatic dependent launch.  wait_prior_grids(): wait for the grids this
 // one depends on (a no-op when it was launched without the attribute); called

@@ -16,7 +16,6 @@ namespace u16wf {
 __global__ void __launch_bounds__(kBlockThreads) check_offsets_kernel(const long long *offsets, long long count,
                                                                       Slot *slot, long long *result) {
     __shared__ unsigned long long s_min;
-    __shared__ bool s_last;
     wait_prior_grids();
     if (threadIdx.x == 0) s_min = ~0ull;
     __syncthreads();
@@ -33,20 +32,13 @@ __global__ void __launch_bounds__(kBlockThreads) check_offsets_kernel(const long
     if (mine != ~0ull) atomicMin(&s_min, mine);
     allow_next_grid();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_min != ~0ull) atomicMin(&slot->min, s_min);
-        __threadfence();
-        const unsigned prev = atomicAdd(&slot->done, 1u);
-        s_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        const unsigned long long g = atomicAdd(&slot->min, 0ull);
+    if (threadIdx.x != 0) return;
+    if (s_min != ~0ull) atomicMin(&slot->min, s_min);
+    if (atomic_add_acq_rel(&slot->done, 1u) == gridDim.x - 1) {
+        const unsigned long long g = ld_acquire(&slot->min);
         *result = (g == ~0ull) ? -1LL : (long long)g;
         slot->min = ~0ull;
         slot->done = 0u;
-        __threadfence();
     }
 }
 

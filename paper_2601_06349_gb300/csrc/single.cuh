@@ -214,49 +214,42 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
 }
 
 // Block minimum, one atomic per block; the last block to finish publishes
-// the first-error index and resets the slot for the next launch.
+// the first-error index and resets the slot for the next launch (the next
+// grid on the stream sees the reset at the kernel boundary).  A grid of one
+// block publishes directly.
 __device__ __forceinline__ void finish_first_bad(const SingleArgs &A, long long my_first, int lane) {
     __shared__ long long s_min[kBlockThreads / 32];
-    __shared__ bool s_last;
     const long long wmin = warp_min_ll(my_first);
     if (lane == 0) s_min[threadIdx.x >> 5] = wmin;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long m = LLONG_MAX;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_min[w] < m ? s_min[w] : m;
-        if (m != LLONG_MAX) atomicMin(&A.slot->min, (unsigned long long)m);
-        __threadfence();
-        const unsigned prev = atomicAdd(&A.slot->done, 1u);
-        s_last = (prev == gridDim.x - 1);
+    if (threadIdx.x != 0) return;
+    long long m = LLONG_MAX;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_min[w] < m ? s_min[w] : m;
+    if (gridDim.x == 1) {
+        // The check's early-exit publications came from this block's warps,
+        // so m already holds them.
+        *A.result = (m < A.n) ? m : A.n;
+        A.slot->min = ~0ull;
+        return;
     }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        const unsigned long long g = atomicAdd(&A.slot->min, 0ull);
+    if (m != LLONG_MAX) atomicMin(&A.slot->min, (unsigned long long)m);
+    if (atomic_add_acq_rel(&A.slot->done, 1u) == gridDim.x - 1) {
+        const unsigned long long g = ld_acquire(&A.slot->min);
         *A.result = (g < (unsigned long long)A.n) ? (long long)g : A.n;
         A.slot->min = ~0ull;
         A.slot->done = 0u;
-        __threadfence();
     }
 }
 
 // List mode: the last block publishes the number of mismatched units and
 // resets the counter for the next launch.
 __device__ __forceinline__ void finish_list(const SingleArgs &A) {
-    __shared__ bool s_last_l;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&A.slot->done, 1u);
-        s_last_l = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (s_last_l && threadIdx.x == 0) {
-        __threadfence();
-        *A.result = (long long)atomicAdd((unsigned long long *)&A.slot->pad1, 0ull);
+    __syncthreads();  // every warp of the block has reserved its positions
+    if (threadIdx.x != 0) return;
+    if (atomic_add_acq_rel(&A.slot->done, 1u) == gridDim.x - 1) {
+        *A.result = (long long)ld_acquire((const unsigned long long *)&A.slot->pad1);
         A.slot->pad1 = 0;
         A.slot->done = 0u;
-        __threadfence();
     }
 }
 
