@@ -323,7 +323,8 @@ typedef struct utf16_server utf16_server;
 typedef struct {
     int64_t hbm_budget_bytes;     /* device arena for admitted batches (>= 1 MiB) */
     int64_t max_batch_strings;    /* strings per launched batch (requests count at most 2 each) */
-    int64_t max_batch_bytes;      /* input bytes per launched batch; also the largest request */
+    int64_t max_batch_bytes;      /* input bytes packed into one launched batch; a longer request is
+                                     launched as a batch of its own */
     int max_inflight_batches;     /* batches between admission and completion (1..64) */
     int64_t staging_bytes;        /* pinned host staging per batch slot */
     int64_t small_request_bytes;  /* requests below this size are packed through staging */
@@ -350,7 +351,8 @@ typedef struct {
     int64_t pending, inflight_batches, arena_used_bytes;
 } utf16_server_stats;
 
-/* Defaults: 4 GiB budget, 65536 strings / 256 MiB per batch, 4 slots, 64 MiB staging, 256 KiB small limit. */
+/* Defaults: 4 GiB budget, 65536 strings / 16 MiB packed per batch, 8 slots, 32 MiB staging per slot,
+ * 256 KiB small limit. */
 int utf16_server_default_options(utf16_server_options *opt);
 /* Allocates the arena, staging and streams on the current device; starts two host threads. */
 int utf16_server_create(const utf16_server_options *opt, utf16_server **server);

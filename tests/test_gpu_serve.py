@@ -184,6 +184,24 @@ def test_oversize_request_rejected(pkg):
             srv.submit(big, big)
 
 
+def test_request_longer_than_batch_target(pkg):
+    """max_batch_bytes bounds packing only: a request longer than it is served
+    as a batch of its own, between packed batches of small requests."""
+    rng = np.random.default_rng(31)
+    reqs = []
+    for i in range(60):
+        n = int(rng.integers(100_000, 300_000)) if i % 10 == 3 else int(rng.integers(1, 2000))
+        reqs.append(workloads.mixed(n, 1e-2, seed=3100 + i))
+    want = _expect(reqs)
+    outs = [np.zeros_like(u) for u in reqs]
+    with pkg.Server(hbm_budget_bytes=64 << 20, max_batch_bytes=64 << 10) as srv:
+        lat, fb = srv.replay(reqs, outs, 0, seed=3)
+        st = srv.stats()
+    for i, (w, f) in enumerate(want):
+        assert np.array_equal(outs[i], w) and fb[i] == f, i
+    assert st["rejected"] == 0 and st["batches"] >= 6
+
+
 def test_aligned_padding_fits_reservation(pkg):
     """Admission reserves arena space for the launch layout, where staged
     requests are packed first and every directly copied request starts at a
