@@ -93,7 +93,7 @@ static bool is_device_memory(const void *p) {
 
 // Device address of `bytes` bytes of page-locked host memory at p, or
 // nullptr when any of them is not page-locked (one mapping end to end).
-static const void *pinned_view(const void *p, int64_t bytes) {
+const void *pinned_view(const void *p, int64_t bytes) {
     cudaPointerAttributes a, b;
     const char *last = (const char *)p + bytes - 1;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {

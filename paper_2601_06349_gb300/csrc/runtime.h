@@ -67,4 +67,8 @@ int run_single(const uint16_t *in, uint16_t *out, int64_t n, int mode, int64_t *
 int run_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t count, int mode, int64_t *first_bad,
               cudaStream_t stream);
 
+// Device address of `bytes` bytes of page-locked, mapped host memory at p, or
+// nullptr when any of them is not (checks both ends of the range).
+const void *pinned_view(const void *p, int64_t bytes);
+
 }  // namespace u16wf

@@ -123,6 +123,53 @@ def test_pinned_and_pageable_in_one_batch(pkg):
         assert fb[i] == f, (i, fb[i], f)
 
 
+def test_large_requests_in_pinned_buffers(pkg):
+    """Large requests whose buffers are pinned are repaired where they are by
+    one fused pass each (out of place, or in place when input and output are
+    the same buffer), at any unit offset, in batches with staged small
+    requests and with large pageable requests that go through the copy
+    engines; a partially overlapping pair takes the copy-engine path."""
+    import torch
+    rng = np.random.default_rng(41)
+    reqs, ins, outs, same = [], [], [], []
+    for i in range(48):
+        kind = i % 4
+        n = int(rng.integers(300_000, 1_200_000)) if kind != 3 else int(rng.integers(1, 3000))
+        u = workloads.mixed(n, float(rng.choice([0.0, 1e-4, 1e-2])), seed=4100 + i)
+        if i % 11 == 0:
+            u[0], u[-1] = 0xDC00, 0xD800  # errors at both ends
+        reqs.append(u)
+        off = int(rng.integers(0, 8))
+        if kind == 0:    # pinned, distinct buffers, odd offsets
+            ins.append(torch.from_numpy(np.concatenate([np.zeros(off, np.uint16), u]).view(np.int16)).pin_memory()[off:])
+            outs.append(torch.zeros(n + 8, dtype=torch.int16).pin_memory()[(off * 3) % 8:][:n])
+        elif kind == 1:  # pinned, one buffer in place
+            t = torch.from_numpy(np.concatenate([np.zeros(off, np.uint16), u]).view(np.int16)).pin_memory()[off:]
+            ins.append(t)
+            outs.append(t)
+        elif kind == 2:  # pageable: copy engines
+            ins.append(u.copy())
+            outs.append(np.zeros_like(u))
+        else:            # small, staged
+            ins.append(torch.from_numpy(u.view(np.int16)).pin_memory())
+            outs.append(torch.zeros(n, dtype=torch.int16).pin_memory())
+    # a partially overlapping pinned pair: output = input shifted by 3 units
+    n = 400_000
+    u = workloads.mixed(n, 1e-2, seed=4199)
+    buf = torch.zeros(n + 3, dtype=torch.int16).pin_memory()
+    buf[:n] = torch.from_numpy(u.view(np.int16))
+    reqs.append(u)
+    ins.append(buf[:n])
+    outs.append(buf[3:])
+    want = _expect(reqs)
+    with pkg.Server(max_inflight_batches=3) as srv:
+        lat, fb = srv.replay(ins, outs, rate_per_s=0, seed=8)
+    for i, (w, f) in enumerate(want):
+        got = outs[i] if isinstance(outs[i], np.ndarray) else outs[i].numpy().view(np.uint16)
+        assert np.array_equal(got, w), (i, first_diff(got, w))
+        assert fb[i] == f, (i, fb[i], f)
+
+
 def test_injected_admission_failures_leave_others_exact(pkg):
     reqs = _requests(200, 14, big=False)
     want = _expect(reqs)
