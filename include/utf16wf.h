@@ -176,13 +176,16 @@ int utf16_get_checked(void);
 /*
  * toWellFormed plus first-error index on HOST buffers.  Blocking: returns
  * when host_out holds the result.
- * When both buffers are page-locked (cudaHostAlloc / cudaHostRegister), one
- * pass of the fused kernel reads and writes them over the host link
- * directly.  Otherwise the string is cut into chunks that are copied to the
- * device, repaired and copied back on three library-owned streams so that
- * the two copy directions and the kernel overlap; each chunk receives its
- * outside neighbours from the host buffer, so the result is that of the
- * whole string (pageable buffers serialise the copies).
+ * When kernels can reach both buffers -- page-locked memory (cudaHostAlloc /
+ * cudaHostRegister), or pageable memory on a device that accesses it
+ * coherently (cudaDevAttrPageableMemoryAccess, e.g. over NVLink-C2C through
+ * the host's page tables; environment UTF16WF_HOST_PAGEABLE_DIRECT=0 turns
+ * this off) -- one pass of the fused kernel reads and writes them over the
+ * host link directly.  Otherwise the string is cut into chunks that are
+ * copied to the device, repaired and copied back on three library-owned
+ * streams so that the two copy directions and the kernel overlap; each chunk
+ * receives its outside neighbours from the host buffer, so the result is that
+ * of the whole string (pageable buffers serialise the copies).
  *   host_in, host_out  [n] host; host_out == host_in is allowed.
  *   first_bad_host     one int64_t on the host, or NULL.
  */

@@ -106,7 +106,16 @@ const void *pinned_view(const void *p, int64_t bytes) {
     return a.devicePointer;
 }
 
-// Both buffers pinned: one fused pass on a library stream.
+const void *host_view(DeviceCtx *ctx, const void *p, int64_t bytes) {
+    if (const void *v = pinned_view(p, bytes)) return v;
+    if (!ctx->pageable_access) return nullptr;
+    const char *e = getenv("UTF16WF_HOST_PAGEABLE_DIRECT");
+    if (e && *e && atoi(e) == 0) return nullptr;
+    return p;
+}
+
+// Both buffers visible to kernels (pinned, or pageable memory on a device
+// that accesses it coherently): one fused pass on a library stream.
 static int host_direct(DeviceCtx *ctx, const uint16_t *din, uint16_t *dout, int64_t n, int64_t *first_bad_host) {
     int rc = ensure_lanes(ctx);
     if (rc) return rc;
@@ -160,8 +169,8 @@ extern "C" int utf16_to_well_formed_host(const uint16_t *host_in, uint16_t *host
 
     std::lock_guard<std::mutex> lk(ctx->stage_mu);
     {
-        const void *din = pinned_view(host_in, n * 2);
-        const void *dout = din ? pinned_view(host_out, n * 2) : nullptr;
+        const void *din = host_view(ctx, host_in, n * 2);
+        const void *dout = din ? (host_out == host_in ? din : host_view(ctx, host_out, n * 2)) : nullptr;
         if (din && dout) return host_direct(ctx, (const uint16_t *)din, (uint16_t *)dout, n, first_bad_host);
     }
     const int64_t chunk = host_chunk_units();

@@ -109,6 +109,12 @@ int get_ctx(DeviceCtx **out) {
         cudaGetLastError();
         return UTF16_ECUDA;
     }
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+        cudaGetLastError();
+        pageable = 0;
+    }
+    c->pageable_access = pageable != 0;
     if (prepare_single_tma() != cudaSuccess) {
         cudaGetLastError();
         return UTF16_ECUDA;

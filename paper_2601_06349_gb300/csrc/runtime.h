@@ -20,6 +20,7 @@ constexpr int kBuckets = 64;  // log2 size buckets for tuned launch configuratio
 struct DeviceCtx {
     int device = 0;
     int sms = 1;
+    bool pageable_access = false;  // kernels may read and write pageable host memory (coherently)
     std::mutex mu;
     Slot *slots = nullptr;  // device pool of kSlotCount slots
     int slots_used = 0;
@@ -70,5 +71,10 @@ int run_batch(const uint16_t *in, uint16_t *out, const int64_t *offsets, int64_t
 // Device address of `bytes` bytes of page-locked, mapped host memory at p, or
 // nullptr when any of them is not (checks both ends of the range).
 const void *pinned_view(const void *p, int64_t bytes);
+
+// Device address of a host range for a kernel: its pinned view, else on a
+// device that accesses pageable memory coherently the address itself
+// (unless UTF16WF_HOST_PAGEABLE_DIRECT=0), else nullptr.
+const void *host_view(DeviceCtx *ctx, const void *p, int64_t bytes);
 
 }  // namespace u16wf

@@ -337,11 +337,8 @@ static void complete_request(utf16_server *S, Request &r, int status) {
 // gave 814-825K requests/s and p99 0.13 ms at 10 % load, all 152 SMs 750K
 // and 0.25 ms, no host passes 748K and 0.32 ms.
 static int host_pass_sms() {
-    static const int v = [] {
-        const char *e = getenv("UTF16WF_SERVE_HOST_PASS_SMS");
-        return (e && *e) ? atoi(e) : 8;
-    }();
-    return v;
+    const char *e = getenv("UTF16WF_SERVE_HOST_PASS_SMS");
+    return (e && *e) ? atoi(e) : 8;
 }
 
 // One large request repaired in the caller's pinned buffers by the fused
@@ -742,14 +739,15 @@ int utf16_server_submit(utf16_server *S, const uint16_t *host_in, uint16_t *host
             cudaGetLastError();
         }
     }
-    // Large requests whose buffers are pinned host memory (the same buffer,
-    // or two that do not overlap) are repaired in place where they are.
+    // Large requests whose buffers kernels can reach (pinned host memory, or
+    // pageable memory on a device that accesses it coherently; the same
+    // buffer, or two that do not overlap) are repaired where they are.
     bool host_pass = false;
     if (large && n > 0 && host_pass_sms() > 0) {
         const uintptr_t x = (uintptr_t)host_in, y = (uintptr_t)host_out, bytes = (uintptr_t)n * 2u;
         const bool overlap = x != y && x < y + bytes && y < x + bytes;
-        const void *vi = overlap ? nullptr : pinned_view(host_in, n * 2);
-        const void *vo = vi ? (host_out == host_in ? vi : pinned_view(host_out, n * 2)) : nullptr;
+        const void *vi = overlap ? nullptr : host_view(S->ctx, host_in, n * 2);
+        const void *vo = vi ? (host_out == host_in ? vi : host_view(S->ctx, host_out, n * 2)) : nullptr;
         if (vi && vo) {
             host_pass = true;
             dev_in = (const uint16_t *)vi;

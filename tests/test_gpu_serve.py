@@ -123,13 +123,17 @@ def test_pinned_and_pageable_in_one_batch(pkg):
         assert fb[i] == f, (i, fb[i], f)
 
 
-def test_large_requests_in_pinned_buffers(pkg):
-    """Large requests whose buffers are pinned are repaired where they are by
-    one fused pass each (out of place, or in place when input and output are
-    the same buffer), at any unit offset, in batches with staged small
-    requests and with large pageable requests that go through the copy
-    engines; a partially overlapping pair takes the copy-engine path."""
+@pytest.mark.parametrize("host_pass_sms", ["", "0"])
+def test_large_requests_in_pinned_buffers(pkg, host_pass_sms):
+    """Large requests whose buffers kernels can reach are repaired where they
+    are by one fused pass each (out of place, or in place when input and
+    output are the same buffer), at any unit offset, in batches with staged
+    small requests; pageable ones too where the device reads pageable memory
+    coherently.  A partially overlapping pair, and every large request with
+    host passes off, goes through the copy engines."""
+    import os
     import torch
+    os.environ["UTF16WF_SERVE_HOST_PASS_SMS"] = host_pass_sms
     rng = np.random.default_rng(41)
     reqs, ins, outs, same = [], [], [], []
     for i in range(48):
@@ -162,8 +166,11 @@ def test_large_requests_in_pinned_buffers(pkg):
     ins.append(buf[:n])
     outs.append(buf[3:])
     want = _expect(reqs)
-    with pkg.Server(max_inflight_batches=3) as srv:
-        lat, fb = srv.replay(ins, outs, rate_per_s=0, seed=8)
+    try:
+        with pkg.Server(max_inflight_batches=3) as srv:
+            lat, fb = srv.replay(ins, outs, rate_per_s=0, seed=8)
+    finally:
+        os.environ.pop("UTF16WF_SERVE_HOST_PASS_SMS", None)
     for i, (w, f) in enumerate(want):
         got = outs[i] if isinstance(outs[i], np.ndarray) else outs[i].numpy().view(np.uint16)
         assert np.array_equal(got, w), (i, first_diff(got, w))

@@ -179,9 +179,14 @@ def test_streams_use_independent_slots(pkg):
         assert int(t.item()) == wants[i]
 
 
+@pytest.mark.parametrize("pageable_direct", ["0", "1"])
 @pytest.mark.parametrize("chunk", [4096, 1 << 20])
-def test_host_pipeline_chunk_edges(pkg, chunk):
+def test_host_pipeline_chunk_edges(pkg, chunk, pageable_direct):
+    """Pageable host buffers: the staged three-stream pipeline (direct passes
+    off), and the direct pass where the device reads pageable memory
+    coherently (else the pipeline again)."""
     os.environ["UTF16WF_HOST_CHUNK_UNITS"] = str(chunk)
+    os.environ["UTF16WF_HOST_PAGEABLE_DIRECT"] = pageable_direct
     try:
         for kind, u in (("shifted", workloads.shifted_alternating(3 * chunk + 77)),
                         ("mixed", workloads.mixed(5 * chunk + 3, 0.01, seed=3)),
@@ -195,6 +200,7 @@ def test_host_pipeline_chunk_edges(pkg, chunk):
             assert np.array_equal(v, want) and fb2 == fb, kind
     finally:
         os.environ.pop("UTF16WF_HOST_CHUNK_UNITS", None)
+        os.environ.pop("UTF16WF_HOST_PAGEABLE_DIRECT", None)
 
 
 def test_host_pipeline_pinned_large(pkg):
