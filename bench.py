@@ -397,13 +397,14 @@ def main():
 
     peak, peak_kind = measured_peaks()
     per_rank_hbm = n * 4 / (ms_per_step * 1e-3) / 1e9
-    traffic = recorded_traffic("single_out_fb_1GiB", tuned.single_variant, tuned.single_units_per_thread)
+    u_eff = tuned.single_units_per_thread or 4  # 0 = chosen by size: 4-vector chunks at this size
+    traffic = recorded_traffic("single_out_fb_1GiB", tuned.single_variant, u_eff)
     roofline = {"bound": "hbm", "achieved": round(per_rank_hbm, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(per_rank_hbm / peak, 4), "peak_kind": peak_kind,
                 "frac_of_nominal_8tbs": round(per_rank_hbm / NOMINAL_HBM_GBS, 4),
                 "traffic": traffic, "algorithmic_bytes_per_launch": n * 4,
                 "kernel": f"fused out-of-place + first-error kernel, variant {tuned.single_variant}, "
-                          f"U={tuned.single_units_per_thread}, blocks/SM={tuned.single_blocks_per_sm or 'max'}"}
+                          f"U={u_eff}, blocks/SM={tuned.single_blocks_per_sm or 'max'}"}
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -221,7 +221,9 @@ typedef struct {
     int single_variant;          /* 0: 128-bit loads; 1: 128-bit loads, next chunk requested before the
                                     current one is processed; 2: TMA bulk copies into a 4-stage
                                     shared-memory ring (16 KiB tiles); repair forms only */
-    int single_units_per_thread; /* 16-byte vectors per thread per warp chunk: 2 or 4 (TMA uses 4) */
+    int single_units_per_thread; /* 16-byte vectors per thread per warp chunk: 2 or 4 (TMA uses 4); 0
+                                    (default): 2 below 40,960 units per SM (about 6.2M units on 152
+                                    SMs), 4 from there on */
     int single_blocks_per_sm;    /* persistent grid = SMs x this; 0 = as many as fit */
     int batch_units_per_thread;  /* 2 or 4 */
     int batch_prefetch;          /* 0 or 1 */

@@ -85,7 +85,8 @@ static bool config_valid(const utf16_config &c) {
            c.check_blocks_per_sm <= 64 && c.inplace_blocks_per_sm >= 0 && c.inplace_blocks_per_sm <= 64 &&
            (c.batch_check_prefetch == 0 || c.batch_check_prefetch == 1) &&
            (c.inplace_unit_stores == 0 || c.inplace_unit_stores == 1) &&
-           (c.single_units_per_thread == 2 || c.single_units_per_thread == 4) && c.single_blocks_per_sm >= 0 &&
+           (c.single_units_per_thread == 0 || c.single_units_per_thread == 2 || c.single_units_per_thread == 4) &&
+           c.single_blocks_per_sm >= 0 &&
            c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
            (c.batch_prefetch == 0 || c.batch_prefetch == 1) && c.batch_blocks_per_sm >= 0 &&
            c.batch_blocks_per_sm <= 64;
@@ -132,7 +133,7 @@ int get_ctx(DeviceCtx **out) {
     cudaStreamDestroy(s);
     utf16_config d;
     d.single_variant = env_int("UTF16WF_SINGLE_VARIANT", kVariantLdg);
-    d.single_units_per_thread = env_int("UTF16WF_SINGLE_U", 4);
+    d.single_units_per_thread = env_int("UTF16WF_SINGLE_U", 0);
     d.single_blocks_per_sm = env_int("UTF16WF_SINGLE_BLOCKS_PER_SM", 0);
     d.batch_units_per_thread = env_int("UTF16WF_BATCH_U", 4);
     d.batch_prefetch = env_int("UTF16WF_BATCH_PREFETCH", 1);
@@ -167,7 +168,13 @@ void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) 
     L.unit_stores = L.mode == kModeInPlace && cfg.inplace_unit_stores != 0;
     // Unit stores exist in the 128-bit-load kernels only.
     if (L.unit_stores && L.variant == kVariantTma) L.variant = kVariantLdg;
-    L.units_per_thread = cfg.single_units_per_thread;
+    // U = 0: by size.  Below about 40 Ki units per SM, 2-vector chunks spread
+    // the string over more warps and SMs (1M units: 3.2-3.5 against 4.4 us
+    // per call back to back; from 8M units on, 4-vector chunks are as fast or
+    // faster, and 23 against 31 us in place at 64M).
+    L.units_per_thread = cfg.single_units_per_thread != 0 ? cfg.single_units_per_thread
+                         : L.n < (long long)ctx->sms * kAutoWideChunkUnitsPerSm ? 2
+                                                                                : 4;
     const bool fb = L.first_bad || L.mode == kModeCheck;
     const bool tma = L.variant == kVariantTma;
     const void *fn = single_kernel_for_occupancy(L.mode, fb, L.units_per_thread, L.variant);
@@ -345,10 +352,14 @@ int utf16_init_device(void) {
     if (rc) return rc;
     for (int mode = 0; mode < 3; ++mode)
         for (int fb = 0; fb < 2; ++fb) {
-            SingleLaunch L;
-            L.mode = mode;
-            L.first_bad = fb != 0;
-            configure_single(ctx, ctx->def, L);
+            for (int u : {2, 4}) {  // both chunk widths, whatever the default picks by size
+                utf16_config c = ctx->def;
+                c.single_units_per_thread = u;
+                SingleLaunch L;
+                L.mode = mode;
+                L.first_bad = fb != 0;
+                configure_single(ctx, c, L);
+            }
             BatchLaunch B;
             B.mode = mode;
             configure_batch(ctx, ctx->def, B);

@@ -17,6 +17,10 @@ constexpr int kSlotCount = 4096;
 constexpr int kHostLanes = 3;
 constexpr int kBuckets = 64;  // log2 size buckets for tuned launch configurations
 
+// Default chunk width by size: strings shorter than this many units per SM
+// take 2-vector chunks, longer ones 4-vector chunks.
+constexpr long long kAutoWideChunkUnitsPerSm = 40960;
+
 struct DeviceCtx {
     int device = 0;
     int sms = 1;
