@@ -204,3 +204,27 @@ def test_autotune_from_length_histogram(pkg):
         assert np.array_equal(fbb, oracle.first_bad_batch(units, offs))
     finally:
         pkg.set_config(saved)
+
+
+def test_chunk_width_by_size(pkg):
+    """The default chunk width (0) is chosen by size: both sides of the switch
+    (40,960 units per SM) give the oracle's results in every mode."""
+    import torch
+    saved = pkg.get_config()
+    try:
+        pkg.set_config(saved, single_units_per_thread=0)
+        assert pkg.get_config().single_units_per_thread == 0
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        for n in (sms * 40960 - 1, sms * 40960 + 3):
+            u = workloads.mixed(n, 1e-3, seed=n % 1000)
+            want, want_fb = oracle.to_well_formed_threads(u), oracle.first_bad_threads(u)
+            d = to_dev(u)
+            out = torch.empty_like(d)
+            _, fb = pkg.to_well_formed_first_bad(d, out)
+            assert np.array_equal(to_host(out), want) and int(fb.item()) == want_fb, n
+            assert pkg.first_error_index_sync(d) == want_fb, n
+            pkg.to_well_formed_(d)
+            assert np.array_equal(to_host(d), want), n
+    finally:
+        pkg.set_config(saved)
+    pkg.check_device_errors()
