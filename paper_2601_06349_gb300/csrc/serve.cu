@@ -109,10 +109,10 @@ struct Request {
     int status = UTF16_OK;
     bool large = false;
     bool direct = false;          // small request whose buffers the GPU reads / writes itself (pinned host memory)
-    bool host_pass = false;       // large request repaired by one kernel in the caller's pinned buffers
+    bool host_pass = false;       // large request repaired by one kernel in the caller's own buffers
     const uint16_t *dev_in = nullptr;   // device view of `in` (direct and host-pass requests)
     uint16_t *dev_out = nullptr;        // device view of `out` (direct and host-pass requests)
-    int64_t dev_off = 0;  // unit offset inside the batch
+    int64_t dev_off = 0;  // unit offset inside the batch (host-pass requests: the index of their string)
 };
 
 // One direct request for the gather / scatter kernels.
@@ -368,7 +368,8 @@ static cudaError_t launch_host_pass(utf16_server *S, BatchSlot &b, const Request
 // Staged small requests are packed first (through the slot's pinned staging
 // buffer); then direct small requests (gathered and scattered by the GPU
 // from and to the callers' pinned buffers) and large ones (copy engines),
-// each at a 16-byte aligned unit offset.  A gap before an aligned request is
+// each at a 16-byte aligned unit offset, and host-pass requests as empty
+// strings (their kernels run after the batch's).  A gap before an aligned request is
 // a padding string of its own, so every request is exactly one string.
 static void launch_batch_slot(utf16_server *S, int si) {
     BatchSlot &b = S->slots[(size_t)si];
