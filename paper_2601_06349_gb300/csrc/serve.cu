@@ -4,20 +4,23 @@
 // utf16_server_submit.  A scheduler thread takes whatever has arrived, admits
 // requests in arrival order against the device arena (a FIFO ring over one
 // allocation of the HBM budget) and launches them as one ragged batch as soon
-// as an in-flight batch slot is free: there is no waiting for a batch to fill.
-// Each batch moves through three streams, ordered by events:
-//   H2D stream      small requests packed in the slot's pinned staging buffer
-//                   (one copy, together with the offsets), large requests
-//                   copied straight from the caller's buffer;
-//   compute stream  in-place batch repair with per-string first-error index
-//                   (one persistent kernel, plus the lengths initialisation);
-//   D2H stream      the packed region and the first-error indices back to the
-//                   staging buffer, large requests straight to the caller.
-// While one batch computes, the next one's input is already on its way and
-// the previous one's output is coming back.  A completion thread waits for
-// batches in launch order, scatters small results to the callers' buffers,
-// records completion time and frees the ring space and the slot, which lets
-// the scheduler admit more requests.
+// as one of the batch slots is free: there is no waiting for a batch to fill.
+// Each slot has its own stream, which carries in order:
+//   - the offsets and the small requests packed in the slot's pinned staging
+//     buffer (one copy), and large requests copied straight from the
+//     caller's buffers;
+//   - the in-place batch repair with per-string first-error index (one
+//     persistent kernel, plus the lengths initialisation);
+//   - one host pass per large request whose buffers kernels can reach: the
+//     single-string kernel on a few SMs, reading and writing the caller's
+//     buffers over the host link;
+//   - the first-error indices and the packed region back to staging, large
+//     copied requests straight to the caller.
+// Batches on different slots overlap, so one batch's input is on its way
+// while another computes and a third comes back.  A completion thread polls
+// the slots' events, completes batches in the order they finish, scatters
+// small results to the callers' buffers, and frees ring space in allocation
+// order and the slot, which lets the scheduler admit more requests.
 //
 // The kernels are the same ragged-batch kernels as utf16_*_batch, so a
 // request's result does not depend on which batch it lands in: every string
