@@ -22,9 +22,9 @@
 // small results to the callers' buffers, and frees ring space in allocation
 // order and the slot, which lets the scheduler admit more requests.
 //
-// The kernels are the same ragged-batch kernels as utf16_*_batch, so a
-// request's result does not depend on which batch it lands in: every string
-// end is a hard boundary.
+// The kernels are the library's own ragged-batch and single-string kernels,
+// so a request's result does not depend on which batch or path it takes:
+// every string end is a hard boundary.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
