@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
     long long my_first = LLONG_MAX;
+    bool filter = true;                    // repair: step-two test on (see process_chunk)
     __shared__ unsigned long long s_best;  // check: this block's smallest published mismatch
     wait_prior_grids();
     if constexpr (MODE == kModeCheck) {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
                 g = __shfl_sync(kFull, g, 0);
                 if (g != ~0ull && (long long)g < cfirst) break;
             }
-            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first, &s_best);
+            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first, &s_best, &filter);
         }
     } else {
         for (long long c = gwarp; c < A.chunks; c += nwarps) {
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
                 g = __shfl_sync(kFull, g, 0);
                 if (g != ~0ull && (long long)g < cfirst) break;
             }
-            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first, &s_best);
+            process_chunk<MODE, FB, ST, U>(A, cfirst, v, lane, my_first, &s_best, &filter);
         }
     }
 
