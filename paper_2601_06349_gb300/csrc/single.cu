@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs 
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
     long long my_first = LLONG_MAX;
-    bool filter = true;                    // repair: step-two test on (see process_chunk)
+    int filter = 0;                        // repair: step-two test on (see process_chunk)
     __shared__ unsigned long long s_best;  // check: this block's smallest published mismatch
     wait_prior_grids();
     if constexpr (MODE == kModeCheck) {

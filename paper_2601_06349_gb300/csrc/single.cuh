@@ -100,13 +100,16 @@ __device__ __forceinline__ void store_chunk_vec(uint16_t *dst, int u, const uint
 }
 
 // Steps 2-5 of the chunk starting at unit cfirst.
-// `filter` (repair modes, warp-uniform): run Section 3.1's step-two test
-// before locating anything; it is on while the warp's last chunk had no
-// mismatch, so that strings with mismatches everywhere skip the test.
+// `filter` (repair modes, warp-uniform): 0 runs Section 3.1's step-two test
+// before locating anything.  A chunk that fails it sets a count of chunks
+// that skip the test, so that strings with mismatches everywhere test only
+// one chunk in kFilterRetry.
+constexpr int kFilterRetry = 16;
+
 template <int MODE, bool FB, int ST, int U>
 __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfirst, const Chunk<U> &ch, int lane,
                                               long long &my_first, unsigned long long *blk_best = nullptr,
-                                              bool *filter = nullptr) {
+                                              int *filter = nullptr) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     const bool edge = (cfirst < 0) || (cfirst + CU > A.n);
     const long long lfirst = cfirst + lane * kUnitsPerVec;  // this lane's first unit
@@ -134,13 +137,19 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
     } else if constexpr (MODE == kModeOut || MODE == kModeInPlace) {
         // Repair: the same test clears a chunk whose pairs all match; it is
         // then copied unchanged (out of place) or left alone (in place).
-        if (filter && *filter && !edge &&
-            !__any_sync(kFull, chunk_step_two<U>(cb, from_prev, unit_is_low(ch.halo), lane) != 0)) {
-            if constexpr (MODE == kModeOut) {
+        if (filter) {
+            if (*filter > 0) {
+                --*filter;
+            } else if (!edge) {
+                if (!__any_sync(kFull, chunk_step_two<U>(cb, from_prev, unit_is_low(ch.halo), lane) != 0)) {
+                    if constexpr (MODE == kModeOut) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) store_chunk_vec<MODE, ST>(dst, u, ch.v[u], false, 0, A.n, 0u);
+                        for (int u = 0; u < U; ++u) store_chunk_vec<MODE, ST>(dst, u, ch.v[u], false, 0, A.n, 0u);
+                    }
+                    return;
+                }
+                *filter = kFilterRetry;
             }
-            return;
         }
     }
     chunk_next_low<U>(cb, unit_is_low(ch.halo), lane, from_next);
@@ -210,9 +219,6 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
                 my_first = p < my_first ? p : my_first;
             }
         }
-    }
-    if constexpr (MODE == kModeOut || MODE == kModeInPlace) {
-        if (filter) *filter = !__any_sync(kFull, any_bad != 0);
     }
     if constexpr (FB && MODE == kModeCheck) {
         // Publish early so that other warps can stop: the block's best so far
