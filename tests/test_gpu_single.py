@@ -332,3 +332,15 @@ def test_host_api_pinned_direct_and_mixed(pkg):
             pageable = np.zeros(n, np.uint16)
             out3, fb3 = pkg.to_well_formed_host(h_in, pageable)
             assert np.array_equal(pageable, want) and fb3 == want_fb, (n, a, "pinned in, pageable out")
+
+
+def test_readme_example(pkg):
+    """The usage example of the README, as written there."""
+    import torch
+    wf = pkg
+    s = torch.tensor([0x48, 0xD800, 0x69, 0xD83D, 0xDE0A], dtype=torch.uint16, device="cuda")
+    out, first_bad = wf.to_well_formed_first_bad(s)
+    assert out.cpu().tolist() == [0x48, 0xFFFD, 0x69, 0xD83D, 0xDE0A]
+    assert first_bad.cpu().tolist() == [1]
+    offsets = torch.tensor([0, 2, 5], dtype=torch.int64, device="cuda")
+    assert wf.first_error_index_batch(s, offsets).cpu().tolist() == [1, 3]
