@@ -323,8 +323,10 @@ def get_checked() -> bool:
 
 def to_well_formed_host(host_in, host_out=None):
     """Repair a host (CPU) buffer through the device; returns (out, first_bad).
-    ``host_in`` / ``host_out``: CPU tensors of 16-bit units (pinned memory
-    gives full copy/compute overlap) or numpy uint16 arrays."""
+    ``host_in`` / ``host_out``: CPU tensors of 16-bit units or numpy uint16
+    arrays.  Pinned buffers, and pageable ones on a device that reads pageable
+    memory coherently (GB300 over NVLink-C2C), take one fused pass over the
+    host link; other buffers a staged copy pipeline."""
     import numpy as np
     if host_out is None:
         if isinstance(host_in, np.ndarray):
