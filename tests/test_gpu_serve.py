@@ -151,9 +151,14 @@ def test_large_requests_in_pinned_buffers(pkg, host_pass_sms):
             t = torch.from_numpy(np.concatenate([np.zeros(off, np.uint16), u]).view(np.int16)).pin_memory()[off:]
             ins.append(t)
             outs.append(t)
-        elif kind == 2:  # pageable: copy engines
-            ins.append(u.copy())
-            outs.append(np.zeros_like(u))
+        elif kind == 2:  # pageable: host passes where the device reads pageable memory, else copy engines
+            if i % 8 == 2:
+                v = u.copy()  # one buffer, in place
+                ins.append(v)
+                outs.append(v)
+            else:
+                ins.append(u.copy())
+                outs.append(np.zeros_like(u))
         else:            # small, staged
             ins.append(torch.from_numpy(u.view(np.int16)).pin_memory())
             outs.append(torch.zeros(n, dtype=torch.int16).pin_memory())
