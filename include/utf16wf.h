@@ -312,15 +312,17 @@ int utf16_selftest_bounded_wait(int64_t limit_ns);
  * `hbm_budget_bytes` (a FIFO ring) and launches whatever has arrived as one
  * ragged batch as soon as one of `max_inflight_batches` batch slots is free
  * -- it never waits for a batch to fill.  Each batch is copied in, repaired
- * in place with the per-string first-error index, and copied out on three
- * streams ordered by events, so transfers of one batch overlap the kernel of
- * the next.  Small requests (< small_request_bytes) are packed through a
- * pinned staging buffer per slot.  A larger request whose buffers are pinned
- * host memory (one buffer, or two that do not overlap) is repaired where it
- * is, by one fused pass of the single-string kernel over the host link on a
- * few SMs (8 by default; environment UTF16WF_SERVE_HOST_PASS_SMS, 0 = off);
- * other large ones are copied straight from and to the caller's buffers
- * (pageable ones synchronously by the CUDA runtime).  With direct_host_access, small
+ * in place with the per-string first-error index, and copied out on its
+ * slot's stream; batches of different slots overlap, so transfers of one
+ * batch overlap the kernels of others.  Small requests (< small_request_bytes)
+ * are packed through a pinned staging buffer per slot.  A larger request
+ * whose buffers kernels can reach (pinned host memory, or pageable memory on a
+ * device that accesses it coherently; one buffer, or two that do not
+ * overlap) is repaired where it is, by one fused pass of the single-string
+ * kernel over the host link on a few SMs (8 by default; environment
+ * UTF16WF_SERVE_HOST_PASS_SMS, 0 = off); other large ones are copied straight
+ * from and to the caller's buffers (pageable ones synchronously by the CUDA
+ * runtime).  With direct_host_access, small
  * requests in pinned buffers are read and written by the GPU directly (one
  * gather and one scatter kernel per batch), which keeps the CPU out of the
  * data path.  Each string of a batch is repaired on
