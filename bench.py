@@ -688,15 +688,20 @@ def serve_measure(torch, wf, count, link_gbs=None):
     outs = [torch.empty_like(t).pin_memory() for t in ins]
     units = int(lens.sum())
 
-    def latencies(lat):
-        return {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
-                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)}
+    def latencies(lat, fb):
+        ok = fb >= 0  # a negative entry is a request's error status (none expected with these sizes)
+        r = {"p50_ms": round(float(np.percentile(lat[ok], 50)) * 1e3, 3),
+             "p99_ms": round(float(np.percentile(lat[ok], 99)) * 1e3, 3)}
+        if not ok.all():
+            r["failed_requests"] = int((~ok).sum())
+        return r
 
     def capacity(lat, fb, wall):
-        assert (fb >= 0).all(), "a request was rejected"
-        span = float(np.max(lat))
-        return {**latencies(lat), "makespan_ms": round(span * 1e3, 3), "call_wall_ms": round(wall * 1e3, 3),
-                "strings_per_s": round(count / span, 1), "input_gbs": round(units * 2 / span / 1e9, 2)}
+        ok = fb >= 0
+        span = float(np.max(lat[ok]))
+        done_units = int(lens[ok].sum())
+        return {**latencies(lat, fb), "makespan_ms": round(span * 1e3, 3), "call_wall_ms": round(wall * 1e3, 3),
+                "strings_per_s": round(int(ok.sum()) / span, 1), "input_gbs": round(done_units * 2 / span / 1e9, 2)}
 
     res = {"requests": count, "units": units, "mean_request_bytes": round(units * 2 / count, 1),
            "hbm_budget_bytes": 4 << 30, "host_buffers": "pinned"}
@@ -724,8 +729,7 @@ def serve_measure(torch, wf, count, link_gbs=None):
             runs = []
             for rep in range(3):  # three Poisson replays; the one with the median p99 is reported
                 lat, fb = srv.replay(ins, outs, rate, seed=11 + rep)
-                assert (fb >= 0).all(), "a request was rejected"
-                runs.append(latencies(lat))
+                runs.append(latencies(lat, fb))
             runs.sort(key=lambda r: r["p99_ms"])
             sweep.append({"rate_frac": frac, "rate_per_s": round(rate, 1), **runs[1],
                           "p99_ms_of_3_runs": [r["p99_ms"] for r in runs]})
@@ -742,7 +746,7 @@ def serve_measure(torch, wf, count, link_gbs=None):
     for frac in (0.25, 0.5):
         rate = frac * cap
         lat, fb = wf.plain_replay(ins, outs, rate, seed=11)
-        plain.append({"rate_frac": frac, "rate_per_s": round(rate, 1), **latencies(lat)})
+        plain.append({"rate_frac": frac, "rate_per_s": round(rate, 1), **latencies(lat, fb)})
     res["plain"] = plain
     return res
 
