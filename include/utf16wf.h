@@ -205,7 +205,12 @@ int utf16_to_well_formed_host(const uint16_t *host_in, uint16_t *host_out, int64
  *   n must not exceed 2^40 units; longer inputs return UTF16_ETOOBIG.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before capturing a
- * stream into a CUDA graph.  Every call shares the one array and keeps the
+ * stream into a CUDA graph.  Under CUDA's lazy module loading (the default)
+ * that first call is also when the library's kernels and the array are loaded
+ * onto the device, so the device footprint grows once, at that call, and never
+ * again: a caller with a fixed footprint makes it at start-up (n == 1 will do).
+ * The chunk width and data path follow the regular entry point's defaults
+ * (2-vector chunks below 40,960 units per SM).  Every call shares the one array and keeps the
  * last call's contents, clearing what must start cleared in stream order:
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race on it and may return wrong first-error indices.
@@ -225,7 +230,8 @@ typedef struct {
                                     (default): 2 below 40,960 units per SM (about 6.2M units on 152
                                     SMs), 4 from there on */
     int single_blocks_per_sm;    /* persistent grid = SMs x this; 0 = as many as fit */
-    int batch_units_per_thread;  /* 2 or 4 */
+    int batch_units_per_thread;  /* 2 or 4; the per-string check (utf16_is_well_formed_batch) reads
+                                    chunks of 1,024 units for 2 and 2,048 units for 4 */
     int batch_prefetch;          /* 0 or 1 */
     int batch_blocks_per_sm;     /* 0 = as many as fit */
     int check_variant;           /* read-only check (utf16_is_well_formed): 0, 1 or 2 as single_variant */
@@ -394,12 +400,20 @@ int utf16_server_destroy(utf16_server *server);
  *   utf16_server_replay  through a serving engine (continuous batching);
  *   utf16_plain_replay   one plain launch per request in arrival order:
  *                        H2D, fused repair + first-error kernel, D2H, wait.
+ *   utf16_plain_replay_streams  the same plain launches pipelined: `streams`
+ *                        (1..64) host threads, each with its own stream and
+ *                        device buffer, take the requests in arrival order,
+ *                        so up to `streams` requests are in flight at once
+ *                        (what overlap alone gives, without batching).
  */
 int utf16_server_replay(utf16_server *server, const uint16_t *const *inputs, uint16_t *const *outputs,
                         const int64_t *lengths, int64_t count, double rate_per_s, uint64_t seed, double *latency_s,
                         int64_t *first_bad);
 int utf16_plain_replay(const uint16_t *const *inputs, uint16_t *const *outputs, const int64_t *lengths, int64_t count,
                        double rate_per_s, uint64_t seed, double *latency_s, int64_t *first_bad);
+int utf16_plain_replay_streams(const uint16_t *const *inputs, uint16_t *const *outputs, const int64_t *lengths,
+                               int64_t count, double rate_per_s, uint64_t seed, int streams, double *latency_s,
+                               int64_t *first_bad);
 
 /*
  * FIFO ring allocator used for serving admission, exposed for reuse and for

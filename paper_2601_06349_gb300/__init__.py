@@ -106,6 +106,8 @@ def _declare(lib):
         "utf16_server_destroy": ([vp], ctypes.c_int),
         "utf16_server_replay": ([vp, vp, vp, vp, i64, ctypes.c_double, ctypes.c_uint64, vp, vp], ctypes.c_int),
         "utf16_plain_replay": ([vp, vp, vp, i64, ctypes.c_double, ctypes.c_uint64, vp, vp], ctypes.c_int),
+        "utf16_plain_replay_streams": ([vp, vp, vp, i64, ctypes.c_double, ctypes.c_uint64, ctypes.c_int, vp, vp],
+                                       ctypes.c_int),
         "utf16_arena_create": ([i64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "utf16_arena_alloc": ([vp, i64], ctypes.c_int64),
         "utf16_arena_free_oldest": ([vp], ctypes.c_int),
@@ -490,7 +492,7 @@ def clock_ns() -> int:
     return lib().utf16_server_clock_ns()
 
 
-def _replay(handle, inputs, outputs, rate_per_s, seed):
+def _replay(handle, inputs, outputs, rate_per_s, seed, streams=0):
     import numpy as np
     count = len(inputs)
     ins = (ctypes.c_void_p * count)()
@@ -504,7 +506,10 @@ def _replay(handle, inputs, outputs, rate_per_s, seed):
         ins[i], outs[i], lens[i] = pa, pb, na
     lat = np.zeros(count, dtype=np.float64)
     fb = np.zeros(count, dtype=np.int64)
-    if handle is None:
+    if handle is None and streams:
+        rc = lib().utf16_plain_replay_streams(ins, outs, lens.ctypes.data, count, float(rate_per_s), seed,
+                                              int(streams), lat.ctypes.data, fb.ctypes.data)
+    elif handle is None:
         rc = lib().utf16_plain_replay(ins, outs, lens.ctypes.data, count, float(rate_per_s), seed,
                                       lat.ctypes.data, fb.ctypes.data)
     else:
@@ -514,10 +519,11 @@ def _replay(handle, inputs, outputs, rate_per_s, seed):
     return lat, fb
 
 
-def plain_replay(inputs, outputs, rate_per_s: float, seed: int = 1):
+def plain_replay(inputs, outputs, rate_per_s: float, seed: int = 1, streams: int = 0):
     """The same replay with one plain launch per request (H2D, fused kernel,
-    D2H, wait), in arrival order."""
-    return _replay(None, inputs, outputs, rate_per_s, seed)
+    D2H, wait), in arrival order: one request at a time (streams = 0), or
+    pipelined over `streams` host threads with a stream each."""
+    return _replay(None, inputs, outputs, rate_per_s, seed, streams)
 
 
 class Arena:

@@ -4,12 +4,12 @@
 // high surrogate has that unit replaced, whatever lies next to it in memory).
 //
 // The flattened unit range [offsets[0], offsets[count]) is read from the
-// device and cut into warp chunks exactly as in the single-string kernel
-// (U slices of 32 vectors of 8 units).  The grid is persistent and each warp
-// owns a contiguous run of chunks, so consecutive chunks of a warp need
-// consecutive entries of `offsets`.
+// device and cut into warp chunks as in the single-string kernel (U slices of
+// 32 vectors of 8 units).  The grid is persistent and each warp owns a
+// contiguous run of chunks, so consecutive chunks of a warp need consecutive
+// entries of `offsets`.
 //
-// Per chunk:
+// Repair (batch_kernel), per chunk:
 //   - fast path: no surrogate in the chunk means nothing can be mismatched,
 //     whatever the string boundaries; out of place the chunk is copied;
 //   - slow path: the warp finds the first string starting at or after the
@@ -18,12 +18,15 @@
 //     start inside the chunk in a per-warp byte map in shared memory, and
 //     applies the pairing rule with "no left neighbour" at a start and "no
 //     right neighbour" just before one;
-//   - per-string first-error index: the chunk's mismatch bits go to shared
-//     memory (one byte per vector, plus a one-bit-per-byte summary from a
-//     ballot), then each lane takes one string of the offsets window and
-//     finds the first set bit from its start.
+//   - per-string first-error index (in place, for the serving engine): the
+//     chunk's mismatch bits go to shared memory (one byte per vector, plus a
+//     one-bit-per-byte summary from a ballot), then each lane takes one string
+//     of the offsets window and finds the first set bit from its start.
+// The per-string check (batch_check_kernel) transposes the chunk's classes
+// into 32-unit bit words per lane and works on words; see its comment below.
 #include <cuda_runtime.h>
 #include <limits.h>
+#include <stdlib.h>
 
 #include "device.cuh"
 #include "internal.h"
@@ -156,21 +159,14 @@ __device__ __forceinline__ int first_mismatch_from(const WarpScratch<U> &ws, con
     return U * kWarpSliceUnits;
 }
 
-// A window of 32 consecutive entries of `offsets` (one per lane), loaded
-// while the previous chunk of the warp was processed (base < 0: none).
-struct OffsetsWindow {
-    long long base = -1;
-    long long off = LLONG_MAX;
-};
-
 template <int MODE, int ST, int U>
 __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long long cfirst, long long lo, long long hi,
                                                     const BatchChunk<U> &ch, int lane, WarpScratch<U> &ws,
-                                                    long long &hint, OffsetsWindow &next_win) {
+                                                    long long &hint) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     const bool edge = (cfirst < lo) || (cfirst + CU > hi);
     const long long lfirst = cfirst + lane * kUnitsPerVec;
-    uint16_t *dst = (MODE == kModeCheck) ? nullptr : A.out + lfirst;
+    uint16_t *dst = A.out + lfirst;
     ChunkBits<U> cb;
     const uint32_t surr = chunk_surrogates<U>(ch.v, cb);
 
@@ -192,22 +188,13 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
     for (int i = lane; i < kStartVecs; i += 32) reinterpret_cast<uint4 *>(ws.starts)[i] = make_uint4(0, 0, 0, 0);
     const long long cend = cfirst + CU;
     // One window of 32 offsets usually covers both the search and the
-    // collection: the one the previous chunk requested for this one (from the
-    // string just before this chunk's first start), else one from the
-    // previous chunk's first string.  Any window whose first entry starts at
-    // or before this chunk's first string will do.
-    // (The check only: in the repair kernels the window's registers cost a
-    // resident block per SM, 70 -> 85 us on 1M strings; the check gains,
-    // 78 -> 76 us.)
-    constexpr bool kWindowAhead = MODE == kModeCheck;
-    long long base, off;
-    if (kWindowAhead && next_win.base >= 0) {
-        base = next_win.base;
-        off = next_win.off;
-    } else {
-        base = hint;
-        off = base + lane <= A.count ? A.offsets[base + lane] : LLONG_MAX;
-    }
+    // collection: one from the previous chunk's first string.  Any window
+    // whose first entry starts at or before this chunk's first string will
+    // do.  (Requesting the next chunk's window ahead, as the per-string check
+    // does, cost these kernels a resident block per SM: 70 -> 85 us on 1M
+    // strings.)
+    long long base = hint;
+    long long off = base + lane <= A.count ? A.offsets[base + lane] : LLONG_MAX;
     long long idx = base + lane;
     unsigned ge = __ballot_sync(kFull, off >= cfirst);
     if (ge == 0) {  // the chunk's strings start beyond this window: search
@@ -221,19 +208,6 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
     const long long base_first = base;
     const long long off_first = off;           // offsets[base_first + lane]
     hint = s_first;
-    // Request the next chunk's window now, so that its latency hides behind
-    // this chunk's work: from the string before the first one starting at or
-    // after this chunk's end (known when this window reaches that far).
-    if constexpr (kWindowAhead) {
-        const unsigned ge_end = __ballot_sync(kFull, off >= cfirst + CU);
-        if (ge_end) {
-            const long long s_next = base + __ffs(ge_end) - 1;
-            next_win.base = s_next > 0 ? s_next - 1 : 0;
-            next_win.off = next_win.base + lane <= A.count ? A.offsets[next_win.base + lane] : LLONG_MAX;
-        } else {
-            next_win.base = -1;
-        }
-    }
     bool simple = true;  // all starts of the chunk lie in the first window
     __syncwarp();
     for (;;) {
@@ -275,13 +249,13 @@ __device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long lon
                 batch_store_vec<MODE, ST>(dst + u * kWarpSliceUnits, fix_vec(ch.v[u], bad_lo, bad_hi), edge, p0, lo,
                                           hi, gather4(bad_lo) | (gather4(bad_hi) << 4));
         }
-        if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
+        if constexpr (MODE == kModeInPlaceFirst) {
             const uint32_t bits8 = gather4(bad_lo) | (gather4(bad_hi) << 4);
             ws.bad[u * 32 + lane] = (uint8_t)bits8;
             nz[u] = __ballot_sync(kFull, bits8 != 0);
         }
     }
-    if constexpr (MODE == kModeCheck || MODE == kModeInPlaceFirst) {
+    if constexpr (MODE == kModeInPlaceFirst) {
         uint32_t any = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) any |= nz[u];
@@ -340,7 +314,6 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
     const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
 
     long long hint = 0;
-    OffsetsWindow next_win;
     if constexpr (PF) {
         BatchChunk<U> nv;
         if (c_begin < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + c_begin * (32LL * U), lo, hi, lane, nv);
@@ -348,22 +321,289 @@ __global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A)
             const BatchChunk<U> v = nv;
             if (c + 1 < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + (c + 1) * (32LL * U), lo, hi, lane, nv);
             const long long cfirst = (vbeg + c * (32LL * U)) * 8 - A.a;
-            process_batch_chunk<MODE, ST, U>(A, cfirst, lo, hi, v, lane, ws, hint, next_win);
+            process_batch_chunk<MODE, ST, U>(A, cfirst, lo, hi, v, lane, ws, hint);
         }
     } else {
         for (long long c = c_begin; c < c_end; ++c) {
             const long long vfirst = vbeg + c * (32LL * U);
             BatchChunk<U> v;
             load_batch_chunk<MODE, U>(A, vin, vfirst, lo, hi, lane, v);
-            process_batch_chunk<MODE, ST, U>(A, vfirst * 8 - A.a, lo, hi, v, lane, ws, hint, next_win);
+            process_batch_chunk<MODE, ST, U>(A, vfirst * 8 - A.a, lo, hi, v, lane, ws, hint);
         }
     }
     allow_next_grid();
 }
 
+// ---------------------------------------------------------------------------
+// Per-string first-error index (the check), word-lane form.
+//
+// After classification each lane packs, per vector, the surrogate bits and
+// the low-surrogate bits of its 8 units (bit k = unit k) into one 16-bit
+// entry of a per-warp table.  Read back four entries at a time, the table
+// gives lane l the units [1024 j + 32 l, +32) of the chunk as 32-bit words,
+// one per 1024 units of chunk (j = 0 for U = 4, j = 0, 1 for U = 8): H (high
+// surrogates) and L (low surrogates).  The 2048-unit chunk halves the
+// per-chunk cost of the offsets window and the lookups per unit (1M strings:
+// 50 -> 43 us).  The string starts inside the
+// chunk become a third word S (one shared atomic OR per start, from a window
+// of the offsets).  The Section 1 rule with every string end as a boundary
+// (Section 3.1) is then word logic in each lane:
+//   Hprev  = H one unit up (bit W-1 of the lane before; lane 0: the unit
+//            before the chunk),  Lnext = L one unit down;
+//   a unit that starts a string has no left neighbour, the unit before it no
+//   right neighbour:  NoRight = S one unit down;
+//   bad    = H & ~(Lnext & ~NoRight) | L & ~(Hprev & ~S).
+// Each lane of the offsets window then takes one string that meets the chunk
+// and finds its first bad unit from max(start, chunk start) in constant time:
+// the word holding that unit (one shuffle), else the first later word with a
+// bad unit (a ballot summary and one more shuffle).  Results go to first_bad
+// with atomicMin, over the string lengths a small kernel writes first.
+
+// Per-warp table and start words of the word-lane check.
+template <int U>
+struct __align__(16) WordScratch {
+    uint16_t cls[U * 32];      // vector v of the chunk: bit k = unit k is a surrogate, bit 8+k = it is a low one
+    uint32_t starts[U * 8];    // word w: bit j set when a string starts at unit 32 w + j of the chunk
+};
+
+// The strings base .. base+31 of the batch, one per lane: its start and end
+// (kFar for lanes past the last string).  kFar stays far from overflow when
+// a chunk position is subtracted from it.
+constexpr long long kFar = LLONG_MAX / 4;
+struct Window {
+    long long base = 0;
+    long long start = kFar;
+    long long end = kFar;
+};
+
+__device__ __forceinline__ void load_window(const BatchArgs &A, long long base, int lane, Window &w) {
+    const long long s = base + lane;
+    w.base = base;
+    w.start = s < A.count ? A.offsets[s] : kFar;
+    w.end = s < A.count ? A.offsets[s + 1] : kFar;
+}
+
+// Position x relative to a chunk [cfirst, cfirst + CU), saturated: -1 before
+// the chunk, CU at its end (the unit after it), CU + 1 beyond.
+template <int CU>
+__device__ __forceinline__ int rel_pos(long long x, long long cfirst) {
+    const long long d = x - cfirst;
+    return d < 0 ? -1 : d > CU ? CU + 1 : (int)d;
+}
+
+// Per-warp state carried from chunk to chunk: a string index at or before the
+// first string of the next chunk, and (when `have_nw`) the window prefetched
+// for the next chunk, which starts with the string holding its first unit.
+struct CheckState {
+    long long hint = 0;
+    Window nw;
+    bool have_nw = false;
+    bool waited = false;
+};
+
+template <int U>
+__device__ __forceinline__ void check_words_chunk(const BatchArgs &A, long long cfirst, const BatchChunk<U> &ch,
+                                                  int lane, WordScratch<U> &ws, CheckState &st) {
+    constexpr int NW = U / 4;            // 32-unit words per lane
+    constexpr int CU = U * kWarpSliceUnits;
+    static_assert(NW == 1 || NW == 2, "chunk width");
+
+    // Classification (high byte only, Section 3.3), packed to the table one
+    // vector at a time so that its registers free at once, and the fast
+    // test.  The barrier after the previous chunk's last reads of the scratch
+    // orders these writes.
+    uint32_t acc = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t hb0 = prmt(ch.v[u].x, ch.v[u].y, 0x7531);
+        const uint32_t hb1 = prmt(ch.v[u].z, ch.v[u].w, 0x7531);
+        const uint32_t sf0 = surrogate_flags(hb0);
+        const uint32_t sf1 = surrogate_flags(hb1);
+        acc |= sf0 | sf1;
+        const uint32_t s8 = pack_flags8(sf0, sf1);
+        const uint32_t l8 = pack_flags8(sf0 & (hb0 << 5), sf1 & (hb1 << 5));
+        ws.cls[32 * u + lane] = (uint16_t)prmt(s8, l8, 0x0073);
+    }
+    if (!__any_sync(kFull, acc != 0)) {  // no surrogate: nothing in the chunk is mismatched
+        if (st.have_nw) st.hint = st.nw.base;  // the window was for this chunk
+        st.have_nw = false;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < NW; ++j) ws.starts[32 * j + lane] = 0u;
+
+    // The chunk's first window: the one prefetched for it, else a search for
+    // the string holding the chunk's first unit.
+    Window w;
+    if (st.have_nw) {
+        w = st.nw;
+    } else {
+        const long long s0 = lower_bound_warp(A.offsets, A.count, st.hint, cfirst + 1, lane) - 1;
+        load_window(A, s0 > 0 ? s0 : 0, lane, w);
+    }
+    st.hint = w.base;
+    st.have_nw = false;
+    const int relS = rel_pos<CU>(w.start, cfirst);
+    const int relE = rel_pos<CU>(w.end, cfirst);
+    __syncwarp();
+
+    // Lane word j covers units [1024 j + 32 lane, +32) of the chunk: table
+    // entries 128 j + 4 lane .. +3.
+    uint32_t H[NW], L[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(&ws.cls[128 * j + 4 * lane]);
+        const uint32_t s32 = prmt(t.x, t.y, 0x6420);
+        L[j] = prmt(t.x, t.y, 0x7531);
+        H[j] = s32 & ~L[j];
+    }
+
+    // String starts in [cfirst, cend) into the start words; a start at cend
+    // (the unit after the chunk) is kept aside.  A chunk whose window's last
+    // string starts inside it walks further windows.  On the way, the first
+    // string that ends beyond cend holds the next chunk's first unit: its
+    // window is requested now, so that its latency hides behind this chunk.
+    uint32_t at_end = 0;
+    int nwin = 1;
+    long long nb = -1;
+    {
+        Window m = w;
+        int mS = relS, mE = relE;
+        for (;;) {
+            if ((unsigned)mS < (unsigned)CU) atomicOr(&ws.starts[mS >> 5], 1u << (mS & 31));
+            at_end |= __ballot_sync(kFull, mS == CU);
+            const unsigned beyond = __ballot_sync(kFull, mE > CU);
+            if (nb < 0 && beyond) nb = m.base + (__ffs(beyond) - 1);
+            if (!(__ballot_sync(kFull, mS < CU) >> 31)) break;
+            load_window(A, m.base + 32, lane, m);
+            mS = rel_pos<CU>(m.start, cfirst);
+            mE = rel_pos<CU>(m.end, cfirst);
+            ++nwin;
+        }
+    }
+    if (nb >= 0) {
+        load_window(A, nb, lane, st.nw);
+        st.have_nw = true;
+    }
+    __syncwarp();
+
+    // Section 1 rule with the string ends, per lane word.  The word before
+    // word j of lane 0 is word j-1 of lane 31 (or the unit before the chunk),
+    // the word after word j of lane 31 is word j+1 of lane 0 (or the unit
+    // after the chunk): a source lane sends the word its destination needs.
+    uint32_t S[NW], bad[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) S[j] = ws.starts[32 * j + lane];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        const uint32_t h_up = __shfl_sync(kFull, (j > 0 && lane == 31) ? H[j > 0 ? j - 1 : 0] : H[j], (lane + 31) & 31);
+        const uint32_t l_dn =
+            __shfl_sync(kFull, (j < NW - 1 && lane == 0) ? L[j < NW - 1 ? j + 1 : j] : L[j], (lane + 1) & 31);
+        const uint32_t s_dn =
+            __shfl_sync(kFull, (j < NW - 1 && lane == 0) ? S[j < NW - 1 ? j + 1 : j] : S[j], (lane + 1) & 31);
+        const uint32_t h_in =
+            (j == 0 && lane == 0) ? (unit_is_high(ch.halo) ? 1u : 0u) : (h_up >> 31);
+        const uint32_t l_in = (j == NW - 1 && lane == 31) ? (unit_is_low(ch.halo) ? 1u : 0u) : l_dn & 1u;
+        const uint32_t s_in = (j == NW - 1 && lane == 31) ? (at_end ? 1u : 0u) : s_dn & 1u;
+        const uint32_t hprev = (H[j] << 1) | h_in;
+        const uint32_t lnext = (L[j] >> 1) | (l_in << 31);
+        const uint32_t noright = (S[j] >> 1) | (s_in << 31);
+        bad[j] = (H[j] & ~(lnext & ~noright)) | (L[j] & ~(hprev & ~S[j]));
+    }
+    // Summary: bit w set when word w (lane w & 31, word w >> 5) has a bad unit.
+    unsigned long long nz = __ballot_sync(kFull, bad[0] != 0);
+    if constexpr (NW == 2) nz |= (unsigned long long)__ballot_sync(kFull, bad[1] != 0) << 32;
+    if (nz == 0) return;
+
+    // first_bad holds the lengths once the grid before this one is done.
+    if (!st.waited) {
+        wait_prior_grids();
+        st.waited = true;
+    }
+    // Each lane's string: its first bad unit from max(start, cfirst) within
+    // the chunk, if that lies before the string's end.
+    Window m = w;
+    int mS = relS, mE = relE;
+    for (int k = 0;;) {
+        const unsigned r = mS > 0 ? (unsigned)mS : 0u;
+        const unsigned wi = (r >> 5) & (32 * NW - 1);  // lanes that take nothing read any word
+        uint32_t b1 = __shfl_sync(kFull, bad[0], wi & 31u);
+        if constexpr (NW == 2) {
+            const uint32_t x = __shfl_sync(kFull, bad[1], wi & 31u);
+            b1 = (wi >> 5) ? x : b1;
+        }
+        b1 &= 0xFFFFFFFFu << (r & 31);
+        const unsigned long long later = wi < 32 * NW - 1 ? nz & (~0ull << (wi + 1)) : 0ull;
+        const unsigned w2 = later ? (unsigned)(__ffsll((long long)later) - 1) : 0u;
+        uint32_t b2 = __shfl_sync(kFull, bad[0], w2 & 31u);
+        if constexpr (NW == 2) {
+            const uint32_t x = __shfl_sync(kFull, bad[1], w2 & 31u);
+            b2 = (w2 >> 5) ? x : b2;
+        }
+        const int q = b1 ? (int)(wi << 5) + __ffs(b1) - 1 : later ? (int)(w2 << 5) + __ffs(b2) - 1 : CU + 2;
+        // (The index is never negative: the unsigned minimum is the same, and
+        // a native reduction.)
+        if (mS < CU && q < mE)
+            atomicMin(reinterpret_cast<unsigned long long *>(&A.first_bad[m.base + lane]),
+                      (unsigned long long)((long long)q - (m.start - cfirst)));
+        if (++k >= nwin) break;
+        load_window(A, m.base + 32, lane, m);
+        mS = rel_pos<CU>(m.start, cfirst);
+        mE = rel_pos<CU>(m.end, cfirst);
+    }
+}
+
+// At least 4 resident blocks per SM: without the bound the 2048-unit form takes
+// 79 registers and 3 blocks; with it 63 and no spills.
+template <int U, bool PF>
+__global__ void __launch_bounds__(kBlockThreads, 4) batch_check_kernel(const BatchArgs A) {
+    __shared__ WordScratch<U> s_scratch[kBlockThreads / 32];
+    const int lane = threadIdx.x & 31;
+    WordScratch<U> &ws = s_scratch[threadIdx.x >> 5];
+    // No wait for the grid before this one here: it is the lengths kernel,
+    // which writes only first_bad and lets this grid start once it has waited
+    // for its own predecessors, so `in` and `offsets` are final.  The wait
+    // comes before the first atomic on first_bad, and before the exit.
+    const long long lo = A.offsets[0];
+    const long long hi = A.offsets[A.count];
+    if (lo >= 0 && hi > lo) {
+        const long long vbeg = (lo + A.a) >> 3;
+        const long long vend = (hi + A.a + 7) >> 3;
+        const long long chunks = (vend - vbeg + 32LL * U - 1) / (32LL * U);
+        const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+        const long long c_begin = gwarp * chunks / nwarps;
+        const long long c_end = (gwarp + 1) * chunks / nwarps;
+        const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
+        CheckState st;
+        if constexpr (PF) {
+            BatchChunk<U> nv;
+            if (c_begin < c_end) load_batch_chunk<kModeCheck, U>(A, vin, vbeg + c_begin * (32LL * U), lo, hi, lane, nv);
+            for (long long c = c_begin; c < c_end; ++c) {
+                const BatchChunk<U> v = nv;
+                if (c + 1 < c_end) load_batch_chunk<kModeCheck, U>(A, vin, vbeg + (c + 1) * (32LL * U), lo, hi, lane, nv);
+                check_words_chunk<U>(A, (vbeg + c * (32LL * U)) * 8 - A.a, v, lane, ws, st);
+            }
+        } else {
+            for (long long c = c_begin; c < c_end; ++c) {
+                const long long vfirst = vbeg + c * (32LL * U);
+                BatchChunk<U> v;
+                load_batch_chunk<kModeCheck, U>(A, vin, vfirst, lo, hi, lane, v);
+                check_words_chunk<U>(A, vfirst * 8 - A.a, v, lane, ws, st);
+            }
+        }
+    }
+    allow_next_grid();
+    wait_prior_grids();
+}
+
 // first_bad[s] = length of string s (the value for a well-formed string).
+// The next grid (the check) may start as soon as this one has waited for
+// its own predecessors: it reads only what those wrote before its first
+// atomic on first_bad, where it waits for this grid.
 __global__ void batch_lengths_kernel(const long long *offsets, long long count, long long *first_bad) {
     wait_prior_grids();
+    allow_next_grid();
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
         first_bad[i] = offsets[i + 1] - offsets[i];
@@ -375,8 +615,15 @@ static const void *batch_ptr(int u, bool pf) {
     return u == 2 ? (const void *)batch_kernel<MODE, ST, 2, false> : (const void *)batch_kernel<MODE, ST, 4, false>;
 }
 
+// The check's chunk: one 32-unit word per lane (1024 units) for the narrow
+// setting, two (2048 units) for the wide one.
+static const void *check_words_ptr(int u, bool pf) {
+    if (pf) return u == 2 ? (const void *)batch_check_kernel<4, true> : (const void *)batch_check_kernel<8, true>;
+    return u == 2 ? (const void *)batch_check_kernel<4, false> : (const void *)batch_check_kernel<8, false>;
+}
+
 static const void *pick_batch(int mode, int st, int u, bool pf) {
-    if (mode == kModeCheck) return batch_ptr<kModeCheck, 16>(u, pf);
+    if (mode == kModeCheck) return check_words_ptr(u, pf);
     if (mode == kModeInPlaceFirst) return batch_ptr<kModeInPlaceFirst, 16>(u, pf);
     if (mode == kModeInPlace) return batch_ptr<kModeInPlace, 16>(u, pf);
     switch (st) {
@@ -416,7 +663,9 @@ cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream) {
     void *args[] = {(void *)&A};
     const long long warps = (long long)L.blocks * (kBlockThreads / 32);
     const long long chunk_units = (L.units_per_thread == 2 ? 2 : 4) * (long long)kWarpSliceUnits;
-    const bool pdl = L.full_occupancy ||
+    // The word-lane check overlaps the lengths kernel before it (it waits only
+    // before its first atomic), which needs the attribute.
+    const bool pdl = L.mode == kModeCheck || L.full_occupancy ||
                      (L.units_hint > 0 && pdl_fits((L.units_hint / chunk_units + warps) / warps, false));
     return launch_kernel(fn, dim3((unsigned)L.blocks), dim3(kBlockThreads), args, 0, stream, pdl);
 }

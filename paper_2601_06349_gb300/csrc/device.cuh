@@ -69,6 +69,15 @@ __device__ __forceinline__ uint32_t spread4(uint32_t x) { return (x * 0x00204081
 // Bits 8k+7 (k < 4) gathered to bits 0..3.
 __device__ __forceinline__ uint32_t gather4(uint32_t flags) { return (((flags >> 7) * 0x00204081u) >> 21) & 0xFu; }
 
+// The byte-lane flags of a vector's 8 units (lo: units 0..3, hi: units 4..7,
+// flag of unit k at bit 8k+7) as byte 3 of the result, bit 24+k = unit k.
+// In (lo >> 4 | hi) units 0..3 sit at bits 3, 11, 19, 27 and units 4..7 at
+// 7, 15, 23, 31; the multiplier 2^0 + 2^7 + 2^14 + 2^21 adds four shifted
+// copies, which put unit k on bit 24+k.  Every partial product lands on a
+// different bit, so the sum has no carries and the other bits of byte 3 stay
+// clear.
+__device__ __forceinline__ uint32_t pack_flags8(uint32_t lo, uint32_t hi) { return ((lo >> 4) | hi) * 0x00204081u; }
+
 // Replace by U+FFFD every unit whose byte-lane flag is set (lo: units 0..3,
 // hi: units 4..7).  prmt with a selector nibble 8+k replicates the sign bit
 // of byte k, so each unit gets an all-ones or all-zeros 16-bit mask.

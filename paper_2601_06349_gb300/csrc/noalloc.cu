@@ -26,6 +26,7 @@
 #include "../../include/utf16wf.h"
 #include "device.cuh"
 #include "internal.h"
+#include "runtime.h"
 
 namespace u16wf {
 
@@ -44,15 +45,22 @@ constexpr int kMaxDevices = 64;
 struct NoAllocDevice {
     bool ready = false;
     Slot *scratch = nullptr;  // device address of g_noalloc_scratch on this device
-    int max_blocks = 0;
+    int sms = 0;
+    // Persistent grid per kernel the call can launch: [in place][4-vector chunks].
+    int max_blocks[2][2] = {{0, 0}, {0, 0}};
 };
 
 static std::mutex g_noalloc_mu;
 static NoAllocDevice g_noalloc_dev[kMaxDevices];
 
+// The data path of each form, as the regular entry points use by default:
+// out of place one chunk at a time, in place with the next chunk's loads in
+// flight.
+static int noalloc_variant(bool in_place) { return in_place ? kVariantLdgPrefetch : kVariantLdg; }
+
 // Set-up, once per device, with that device current: the device address of
 // the array (host code cannot use the symbol itself) and the persistent grid
-// size.  None of these calls allocates.
+// size of every kernel the call can launch.  None of these calls allocates.
 static int noalloc_setup(NoAllocDevice **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -68,19 +76,26 @@ static int noalloc_setup(NoAllocDevice **out) {
             cudaGetLastError();
             return UTF16_ECUDA;
         }
-        int sms = 0, per_sm = 0;
+        int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             cudaGetLastError();
             return UTF16_ECUDA;
         }
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, single_kernel_for_occupancy(kModeOut, true, 4),
-                                                          kBlockThreads, 0) != cudaSuccess ||
-            per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
+        for (int ip = 0; ip < 2; ++ip) {
+            for (int wide = 0; wide < 2; ++wide) {
+                const void *fn = single_kernel_for_occupancy(ip ? kModeInPlace : kModeOut, true, wide ? 4 : 2,
+                                                             noalloc_variant(ip != 0));
+                int per_sm = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlockThreads, 0) != cudaSuccess ||
+                    per_sm < 1) {
+                    cudaGetLastError();
+                    per_sm = 1;
+                }
+                d.max_blocks[ip][wide] = sms * per_sm;
+            }
         }
         d.scratch = ptr;
-        d.max_blocks = sms * per_sm;
+        d.sms = sms;
         d.ready = true;
     }
     *out = &d;
@@ -137,10 +152,17 @@ extern "C" int utf16_to_well_formed_first_bad_noalloc(const uint16_t *in, uint16
     L.in = in;
     L.out = out;
     L.n = n;
-    L.mode = (in == out) ? kModeInPlace : kModeOut;
+    const bool in_place = in == out;
+    L.mode = in_place ? kModeInPlace : kModeOut;
     L.first_bad = true;
-    L.units_per_thread = 4;
-    L.max_blocks = d->max_blocks;
+    L.variant = noalloc_variant(in_place);
+    // Chunk width by size, as the regular entry points choose it: 2-vector
+    // chunks below kAutoWideChunkUnitsPerSm units per SM spread a short string
+    // over more SMs.
+    const bool wide = n >= (int64_t)d->sms * kAutoWideChunkUnitsPerSm;
+    L.units_per_thread = wide ? 4 : 2;
+    L.max_blocks = d->max_blocks[in_place ? 1 : 0][wide ? 1 : 0];
+    L.full_occupancy = true;
     L.slot = slot;
     L.result = on_device ? (long long *)first_bad : &slot->result;
     L.lead = 0;

@@ -173,3 +173,94 @@ extern "C" int utf16_plain_replay(const uint16_t *const *inputs, uint16_t *const
     cudaFreeHost(h_first);
     return rc;
 }
+
+// One plain launch per request, pipelined: `streams` host threads each own a
+// stream, a device buffer and a pinned first-error cell.  Each takes the next
+// request in arrival order, waits for its arrival time, and runs H2D, the
+// fused in-place repair + first-error kernel and D2H on its stream, then waits
+// for them; up to `streams` requests are in flight at once.
+extern "C" int utf16_plain_replay_streams(const uint16_t *const *inputs, uint16_t *const *outputs,
+                                          const int64_t *lengths, int64_t count, double rate_per_s, uint64_t seed,
+                                          int streams, double *latency_s, int64_t *first_bad) {
+    if (count < 0 || streams < 1 || streams > 64 ||
+        (count > 0 && (!inputs || !outputs || !lengths || !latency_s || !first_bad)))
+        return UTF16_EINVAL;
+    int64_t max_n = 1;
+    for (int64_t i = 0; i < count; ++i) {
+        if (lengths[i] < 0) return UTF16_EINVAL;
+        max_n = lengths[i] > max_n ? lengths[i] : max_n;
+    }
+    struct Lane {
+        uint16_t *d = nullptr;
+        int64_t *d_first = nullptr, *h_first = nullptr;
+        cudaStream_t s = nullptr;
+    };
+    std::vector<Lane> lanes((size_t)streams);
+    int rc = UTF16_OK;
+    for (Lane &l : lanes) {
+        if (cudaMalloc((void **)&l.d, (size_t)max_n * 2u) != cudaSuccess ||
+            cudaMalloc((void **)&l.d_first, sizeof(int64_t)) != cudaSuccess ||
+            cudaHostAlloc((void **)&l.h_first, sizeof(int64_t), cudaHostAllocDefault) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            rc = UTF16_ENOMEM;
+            break;
+        }
+    }
+    if (rc == UTF16_OK) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const int64_t start = utf16_server_clock_ns() + 1000000;
+        const std::vector<int64_t> at = arrival_times(count, rate_per_s, seed, start);
+        std::atomic<int64_t> next{0};
+        std::atomic<int> err{UTF16_OK};
+        std::vector<std::thread> workers;
+        for (int w = 0; w < streams; ++w) {
+            workers.emplace_back([&, w] {
+                cudaSetDevice(dev);
+                Lane &l = lanes[(size_t)w];
+                for (;;) {
+                    const int64_t i = next.fetch_add(1);
+                    if (i >= count || err.load() != UTF16_OK) return;
+                    wait_until(at[(size_t)i]);
+                    const int64_t n = lengths[i];
+                    int r = UTF16_OK;
+                    if (n > 0) {
+                        if (cudaMemcpyAsync(l.d, inputs[i], (size_t)n * 2u, cudaMemcpyHostToDevice, l.s) !=
+                            cudaSuccess)
+                            r = UTF16_ECUDA;
+                        if (r == UTF16_OK) r = run_single(l.d, l.d, n, kModeInPlace, l.d_first, l.s, 0, 0);
+                        if (r == UTF16_OK &&
+                            (cudaMemcpyAsync(outputs[i], l.d, (size_t)n * 2u, cudaMemcpyDeviceToHost, l.s) !=
+                                 cudaSuccess ||
+                             cudaMemcpyAsync(l.h_first, l.d_first, sizeof(int64_t), cudaMemcpyDeviceToHost, l.s) !=
+                                 cudaSuccess ||
+                             cudaStreamSynchronize(l.s) != cudaSuccess))
+                            r = UTF16_ECUDA;
+                        first_bad[i] = r == UTF16_OK ? *l.h_first : r;
+                    } else {
+                        first_bad[i] = 0;
+                    }
+                    latency_s[i] = (double)(utf16_server_clock_ns() - at[(size_t)i]) * 1e-9;
+                    if (r != UTF16_OK) {
+                        int expect = UTF16_OK;
+                        err.compare_exchange_strong(expect, r);
+                    }
+                }
+            });
+        }
+        for (std::thread &t : workers) t.join();
+        rc = err.load();
+    }
+    for (Lane &l : lanes) {
+        if (l.s) {
+            cudaStreamSynchronize(l.s);
+            cudaStreamDestroy(l.s);
+        }
+        if (l.d) cudaFree(l.d);
+        if (l.d_first) cudaFree(l.d_first);
+        if (l.h_first) cudaFreeHost(l.h_first);
+    }
+    cudaGetLastError();
+    return rc;
+}

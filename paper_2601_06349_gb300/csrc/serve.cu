@@ -732,15 +732,14 @@ int utf16_server_submit(utf16_server *S, const uint16_t *host_in, uint16_t *host
     const uint16_t *dev_in = nullptr;
     uint16_t *dev_out = nullptr;
     if (S->opt.direct_host_access && n > 0 && !large) {
-        cudaPointerAttributes ai, ao;
-        if (cudaPointerGetAttributes(&ai, host_in) == cudaSuccess && ai.type == cudaMemoryTypeHost &&
-            ai.devicePointer && cudaPointerGetAttributes(&ao, host_out) == cudaSuccess &&
-            ao.type == cudaMemoryTypeHost && ao.devicePointer) {
+        // Both ends of each range must lie in one page-locked mapping: a
+        // buffer that starts in pinned memory and runs past it is staged.
+        const void *vi = pinned_view(host_in, n * 2);
+        const void *vo = vi ? (host_out == host_in ? vi : pinned_view(host_out, n * 2)) : nullptr;
+        if (vi && vo) {
             direct = true;
-            dev_in = (const uint16_t *)ai.devicePointer;
-            dev_out = (uint16_t *)ao.devicePointer;
-        } else {
-            cudaGetLastError();
+            dev_in = (const uint16_t *)vi;
+            dev_out = (uint16_t *)vo;
         }
     }
     // Large requests whose buffers kernels can reach (pinned host memory, or

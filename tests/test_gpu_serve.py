@@ -234,6 +234,13 @@ def test_plain_replay_matches(pkg):
     lat, fb = pkg.plain_replay(reqs, outs, rate_per_s=0, seed=5)
     for i, (w, f) in enumerate(want):
         assert np.array_equal(outs[i], w) and fb[i] == f, i
+    # pipelined over several streams: the same results, every request completed
+    for streams in (1, 4, 8):
+        outs = [np.zeros_like(u) for u in reqs]
+        lat, fb = pkg.plain_replay(reqs, outs, rate_per_s=0, seed=5, streams=streams)
+        for i, (w, f) in enumerate(want):
+            assert np.array_equal(outs[i], w) and fb[i] == f, (streams, i)
+        assert np.all(lat >= 0)
 
 
 def test_oversize_request_rejected(pkg):

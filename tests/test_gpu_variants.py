@@ -109,6 +109,28 @@ def test_batch_split_pairs_at_every_start_position(pkg, u, pf, bps):
     pkg.check_device_errors()
 
 
+@pytest.mark.parametrize("u,pf,bps", BATCH)
+def test_batch_window_straddles_chunk_end(pkg, u, pf, bps):
+    """The per-string check reads windows of 32 offsets.  With strings of
+    q = chunk/32 units and one of 2q per chunk, a chunk holds more than 31
+    starts, its first window ends just before the chunk's end and the next
+    window starts just after it: the string holding the next chunk's first
+    unit is the last of the earlier window.  A lone low surrogate 6 units into
+    every chunk lies in that string."""
+    pkg.set_config(batch_units_per_thread=u, batch_prefetch=pf, batch_blocks_per_sm=bps, batch_check_prefetch=pf)
+    from test_gpu_batch import _run_all_forms
+    cu = 256 * u
+    q = cu // 32
+    chunks = 40_000  # several chunks per warp of the persistent grid, so prefetched windows are used
+    lens = np.array([q] * 31 + [2 * q] + ([q] * 30 + [2 * q]) * (chunks - 1), np.int64)
+    offs = workloads.offsets_from_lengths(lens)
+    units = np.full(int(offs[-1]) + 8, 0x41, np.uint16)
+    units[np.arange(1, chunks) * cu + 6] = 0xDC00
+    units[np.arange(1, chunks, 7) * cu - 1] = 0xD800  # and some high surrogates cut by the chunk end
+    _run_all_forms(pkg, units, offs, 0, 0, f"straddle u={u} pf={pf}")
+    pkg.check_device_errors()
+
+
 def test_autotuner_choice_is_correct(pkg):
     import torch
     u = workloads.mixed(64 << 20, 1e-2, seed=51)

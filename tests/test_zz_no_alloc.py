@@ -1,19 +1,30 @@
-"""The no-allocation entry point (for callers that cannot let a library call
+"""The no-allocation entry point, for callers that cannot let a library call
 cudaMalloc: device memory reserved up front by a host framework, allocation
-forbidden after start-up, or a fixed device footprint).  It keeps its scratch
-in an array compiled into the library.  This test calls it through the C ABI
-and checks it against the regular fused entry point, on two calls in a row
-(the shared scratch must be cleared between them), with device and host
-first-error pointers.  Collected last so that a run stopping at the first
-failure has already run every other test."""
+forbidden after start-up, or a device footprint that must not change.  It
+keeps its first-error scratch in an array compiled into the library and
+shared by every call.
+
+Through the C ABI, against the CPU oracle and the regular fused entry point:
+two calls in a row (the shared scratch must be cleared between them), with
+device and host first-error pointers, out of place and in place (in == out),
+and the sizes 0, 1, 7 and both chunk widths.  A fresh process calls it
+before any other entry point of the library and checks that repeated calls
+leave the device's free memory unchanged.  Collected last, so that a run
+stopping at the first failure has already run every other test."""
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _lib():
@@ -27,37 +38,80 @@ def _lib():
 
 def _dev(a):
     import torch
-    return torch.from_numpy(a.view(np.int16)).cuda()
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).cuda()
 
 
-def test_no_alloc_matches_regular_entry_point_twice():
+def _host(t):
+    return t.cpu().numpy().view(np.uint16)
+
+
+def _inputs():
+    big = workloads.mixed(3_000_017, 1e-2, seed=41)         # first error early; 2-vector chunks
+    clean = workloads.mixed(2_000_003, 0.0, seed=42)        # one lone low surrogate near the end
+    clean[1_999_000] = 0xDC00
+    wide = workloads.mixed(8_000_011, 1e-6, seed=43)        # above 40,960 units per SM: 4-vector chunks
+    return [big, clean, wide]
+
+
+def test_no_alloc_matches_oracle_and_regular_entry_point_twice():
     import torch
     pkg, lib = _lib()
     stream = torch.cuda.current_stream()
     h = ctypes.c_void_p(stream.cuda_stream)
-    inputs = [workloads.mixed(3_000_017, 1e-2, seed=41),   # first error early
-              workloads.mixed(2_000_003, 0.0, seed=42)]    # well formed: first_bad = n
-    inputs[1][1_999_000] = 0xDC00                          # one lone low surrogate near the end
-    for u in inputs:
+    for u in _inputs():
+        want = oracle.to_well_formed(u)
+        want_fb = oracle.first_bad(u)
         d_in = _dev(u)
         ref_out = torch.empty_like(d_in)
         ref_fb = torch.full((1,), -1, dtype=torch.int64, device="cuda")
         assert lib.utf16_to_well_formed_first_bad(d_in.data_ptr(), ref_out.data_ptr(), u.size,
                                                   ref_fb.data_ptr(), h) == 0
-        out = torch.empty_like(d_in)
-        fb = torch.full((1,), -1, dtype=torch.int64, device="cuda")
-        assert lib.utf16_to_well_formed_first_bad_noalloc(d_in.data_ptr(), out.data_ptr(), u.size,
-                                                          fb.data_ptr(), h) == 0
-        torch.cuda.synchronize()
-        assert torch.equal(out, ref_out)
-        assert int(fb.item()) == int(ref_fb.item())
-        # host first-error pointer: the call waits and returns the index
-        out2 = torch.empty_like(d_in)
-        v = ctypes.c_int64(-1)
-        assert lib.utf16_to_well_formed_first_bad_noalloc(d_in.data_ptr(), out2.data_ptr(), u.size,
-                                                          ctypes.addressof(v), h) == 0
-        assert v.value == int(ref_fb.item())
-        assert torch.equal(out2, ref_out)
+        for _ in range(2):  # two calls in a row on the shared scratch
+            out = torch.empty_like(d_in)
+            fb = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+            assert lib.utf16_to_well_formed_first_bad_noalloc(d_in.data_ptr(), out.data_ptr(), u.size,
+                                                              fb.data_ptr(), h) == 0
+            torch.cuda.synchronize()
+            assert np.array_equal(_host(out), want)
+            assert int(fb.item()) == want_fb
+            assert torch.equal(out, ref_out) and int(ref_fb.item()) == want_fb
+            # host first-error pointer: the call waits and returns the index
+            out2 = torch.empty_like(d_in)
+            v = ctypes.c_int64(-1)
+            assert lib.utf16_to_well_formed_first_bad_noalloc(d_in.data_ptr(), out2.data_ptr(), u.size,
+                                                              ctypes.addressof(v), h) == 0
+            assert v.value == want_fb
+            assert np.array_equal(_host(out2), want)
+
+
+def test_no_alloc_in_place_and_small_sizes():
+    import torch
+    _, lib = _lib()
+    stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p(stream.cuda_stream)
+    cases = [np.array([0xDC00], np.uint16), np.array([0x41], np.uint16),
+             np.array([0xD800, 0xDC00, 0xD800, 0x41, 0xDC00, 0xDBFF, 0xDFFF], np.uint16),
+             np.array([0x41, 0x42, 0xD83D, 0xDE0A, 0x43, 0x44, 0xD800], np.uint16)] + _inputs()
+    for u in cases:
+        want = oracle.to_well_formed(u)
+        want_fb = oracle.first_bad(u)
+        for _ in range(2):
+            buf = _dev(u)  # in place: in == out
+            fb = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+            assert lib.utf16_to_well_formed_first_bad_noalloc(buf.data_ptr(), buf.data_ptr(), u.size,
+                                                              fb.data_ptr(), h) == 0
+            torch.cuda.synchronize()
+            assert np.array_equal(_host(buf), want), u.size
+            assert int(fb.item()) == want_fb, u.size
+            out = torch.empty_like(buf)
+            v = ctypes.c_int64(-1)
+            assert lib.utf16_to_well_formed_first_bad_noalloc(_dev(u).data_ptr(), out.data_ptr(), u.size,
+                                                              ctypes.addressof(v), h) == 0
+            assert np.array_equal(_host(out), want) and v.value == want_fb, u.size
+    # n == 0 with a device first-error pointer: written in stream order
+    fb = torch.full((1,), 123, dtype=torch.int64, device="cuda")
+    assert lib.utf16_to_well_formed_first_bad_noalloc(None, None, 0, fb.data_ptr(), h) == 0
+    assert int(fb.item()) == 0
 
 
 def test_no_alloc_rejects_bad_arguments():
@@ -68,3 +122,41 @@ def test_no_alloc_rejects_bad_arguments():
                                                       ctypes.addressof(v), None) == -8
     assert lib.utf16_to_well_formed_first_bad_noalloc(None, None, 0, ctypes.addressof(v), None) == 0
     assert v.value == 0
+
+
+_FRESH = r"""
+import ctypes, sys
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+import oracle, workloads
+import paper_2601_06349_gb300 as pkg
+torch.cuda.set_device(0)
+u = workloads.mixed(4_000_037, 1e-2, seed=44)
+want, want_fb = oracle.to_well_formed(u), oracle.first_bad(u)
+d_in = torch.from_numpy(u.view(np.int16)).cuda()
+outs = [torch.empty_like(d_in) for _ in range(4)]
+fbs = [torch.full((1,), -1, dtype=torch.int64, device="cuda") for _ in range(4)]
+torch.cuda.synchronize()
+fn = pkg.lib().utf16_to_well_formed_first_bad_noalloc  # no other entry point of the library runs in this process
+fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+fn.restype = ctypes.c_int
+free = []
+for k in range(4):
+    assert fn(d_in.data_ptr(), outs[k].data_ptr(), u.size, fbs[k].data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    free.append(torch.cuda.mem_get_info()[0])
+for k in range(4):
+    assert np.array_equal(outs[k].cpu().numpy().view(np.uint16), want), k
+    assert int(fbs[k].item()) == want_fb, k
+# the first call may load the module (lazy loading); after it nothing changes
+assert free[1] == free[2] == free[3], free
+print("fresh ok", want_fb, free)
+"""
+
+
+def test_no_alloc_first_call_in_a_fresh_process():
+    r = subprocess.run([sys.executable, "-c", _FRESH.format(root=ROOT)], capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "fresh ok" in r.stdout
