@@ -48,6 +48,8 @@ struct SingleLaunch {
 
 cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream);
 const void *single_kernel_for_occupancy(int mode, bool fb, int u, int variant = kVariantLdg);
+// In-place repair on bit words (single_words.cu), chunks of u = 4 or 8 slices.
+const void *inplace_words_kernel_for(bool fb, int u, bool pf);
 size_t single_tma_smem_bytes();
 cudaError_t prepare_single_tma();
 unsigned int read_and_clear_tma_timeout();
