@@ -230,9 +230,10 @@ typedef struct {
                                     (default): 2 below 40,960 units per SM (about 6.2M units on 152
                                     SMs), 4 from there on */
     int single_blocks_per_sm;    /* persistent grid = SMs x this; 0 = as many as fit */
-    int batch_units_per_thread;  /* 2 or 4; the per-string check (utf16_is_well_formed_batch) reads
-                                    chunks of 1,024 units for 2 and 2,048 units for 4 */
-    int batch_prefetch;          /* 0 or 1 */
+    int batch_units_per_thread;  /* batch chunk: 2 = 1,024 units, 4 = 2,048 units; 0 (default) = by form:
+                                    1,024 out of place, 2,048 in place and for the per-string check */
+    int batch_prefetch;          /* batch repair: 1 = next chunk requested before the current one is
+                                    processed; 0 (default) */
     int batch_blocks_per_sm;     /* 0 = as many as fit */
     int check_variant;           /* read-only check (utf16_is_well_formed): 0, 1 or 2 as single_variant */
     int inplace_unit_stores;     /* in-place repair of single strings: 0 = store each 16-byte block that

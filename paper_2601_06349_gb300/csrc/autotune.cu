@@ -310,6 +310,10 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
             }
         }
     }
+    // A 1024-unit chunk is what the out-of-place repair takes by default:
+    // store "by mode", so that the other batch forms keep their own width
+    // (2048 units for the check and in place).
+    if (winner.batch_units_per_thread == 2) winner.batch_units_per_thread = 0;
     // The per-string check: next chunk in flight or not, with the winner's
     // other settings (its results go to a scratch array).
     {

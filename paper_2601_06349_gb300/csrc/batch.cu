@@ -4,26 +4,13 @@
 // high surrogate has that unit replaced, whatever lies next to it in memory).
 //
 // The flattened unit range [offsets[0], offsets[count]) is read from the
-// device and cut into warp chunks as in the single-string kernel (U slices of
-// 32 vectors of 8 units).  The grid is persistent and each warp owns a
-// contiguous run of chunks, so consecutive chunks of a warp need consecutive
-// entries of `offsets`.
-//
-// Repair (batch_kernel), per chunk:
-//   - fast path: no surrogate in the chunk means nothing can be mismatched,
-//     whatever the string boundaries; out of place the chunk is copied;
-//   - slow path: the warp finds the first string starting at or after the
-//     chunk by a 32-way search over `offsets` (a window of 32 consecutive
-//     entries from the previous chunk's answer first), marks every string
-//     start inside the chunk in a per-warp byte map in shared memory, and
-//     applies the pairing rule with "no left neighbour" at a start and "no
-//     right neighbour" just before one;
-//   - per-string first-error index (in place, for the serving engine): the
-//     chunk's mismatch bits go to shared memory (one byte per vector, plus a
-//     one-bit-per-byte summary from a ballot), then each lane takes one string
-//     of the offsets window and finds the first set bit from its start.
-// The per-string check (batch_check_kernel) transposes the chunk's classes
-// into 32-unit bit words per lane and works on words; see its comment below.
+// device and cut into warp chunks of U slices of 32 vectors of 8 units
+// (U = 4 or 8: 1024 or 2048 units).  The grid is persistent and each warp
+// owns a contiguous run of chunks, so consecutive chunks of a warp need
+// consecutive entries of `offsets`.  One kernel (batch_words_kernel) serves
+// every form: out of place, in place, the per-string first-error index (the
+// check), and in place with the per-string index (the serving engine); the
+// per-chunk steps are described above words_chunk() below.
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <stdlib.h>
@@ -131,240 +118,65 @@ __device__ __forceinline__ void batch_store_vec(uint16_t *d, const uint4 &f, boo
     }
 }
 
-// Per-warp shared scratch of the slow path.
-template <int U>
-struct __align__(16) WarpScratch {
-    uint8_t starts[U * kWarpSliceUnits + 16];  // 0x80 at r when a string starts at unit cfirst + r (r <= CU)
-    uint8_t bad[U * 32];                        // per-string first-error modes: mismatch bits of vector 32u + lane
-};
-
-// Per-string first-error modes: the chunk's mismatched units as one bit per
-// unit (ws.bad, byte 32u + lane = vector u of that lane, bit k = unit k)
-// plus a summary with one bit per byte (bit lane of nz[u]).  Returns the
-// first unit index >= r (0 <= r < CU) of the chunk with its bit set, or CU.
-template <int U>
-__device__ __forceinline__ int first_mismatch_from(const WarpScratch<U> &ws, const uint32_t (&nz)[U], int r) {
-    const int b0 = r >> 3;
-    const uint32_t m0 = ws.bad[b0] & (0xFFu << (r & 7));
-    if (m0) return (b0 << 3) + __ffs(m0) - 1;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int from = b0 + 1 - 32 * u;  // first byte of word u after byte b0
-        uint32_t m = from >= 32 ? 0u : from > 0 ? nz[u] & (0xFFFFFFFFu << from) : nz[u];
-        if (m) {
-            const int b = 32 * u + __ffs(m) - 1;
-            return (b << 3) + __ffs(ws.bad[b]) - 1;
-        }
-    }
-    return U * kWarpSliceUnits;
-}
-
-template <int MODE, int ST, int U>
-__device__ __forceinline__ void process_batch_chunk(const BatchArgs &A, long long cfirst, long long lo, long long hi,
-                                                    const BatchChunk<U> &ch, int lane, WarpScratch<U> &ws,
-                                                    long long &hint) {
-    constexpr long long CU = (long long)U * kWarpSliceUnits;
-    const bool edge = (cfirst < lo) || (cfirst + CU > hi);
-    const long long lfirst = cfirst + lane * kUnitsPerVec;
-    uint16_t *dst = A.out + lfirst;
-    ChunkBits<U> cb;
-    const uint32_t surr = chunk_surrogates<U>(ch.v, cb);
-
-    if (!__any_sync(kFull, surr != 0)) {
-        if constexpr (MODE == kModeOut) {
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                batch_store_vec<MODE, ST>(dst + u * kWarpSliceUnits, ch.v[u], edge, lfirst + u * kWarpSliceUnits, lo,
-                                          hi, 0u);
-        }
-        return;
-    }
-
-    // String starts in [cfirst, cfirst + CU] as a byte map (0x80 per start).
-    // The barrier orders the previous chunk's reads of the scratch before
-    // these writes.
-    constexpr int kStartVecs = (int)(CU + 16) / 16;
-    __syncwarp();
-    for (int i = lane; i < kStartVecs; i += 32) reinterpret_cast<uint4 *>(ws.starts)[i] = make_uint4(0, 0, 0, 0);
-    const long long cend = cfirst + CU;
-    // One window of 32 offsets usually covers both the search and the
-    // collection: one from the previous chunk's first string.  Any window
-    // whose first entry starts at or before this chunk's first string will
-    // do.  (Requesting the next chunk's window ahead, as the per-string check
-    // does, cost these kernels a resident block per SM: 70 -> 85 us on 1M
-    // strings.)
-    long long base = hint;
-    long long off = base + lane <= A.count ? A.offsets[base + lane] : LLONG_MAX;
-    long long idx = base + lane;
-    unsigned ge = __ballot_sync(kFull, off >= cfirst);
-    if (ge == 0) {  // the chunk's strings start beyond this window: search
-        base = lower_bound_warp(A.offsets, A.count, base + 32, cfirst, lane);
-        idx = base + lane;
-        off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
-        ge = __ballot_sync(kFull, off >= cfirst);
-    }
-    const int fs_lane = __ffs(ge) - 1;
-    const long long s_first = base + fs_lane;  // first string starting at or after cfirst
-    const long long base_first = base;
-    const long long off_first = off;           // offsets[base_first + lane]
-    hint = s_first;
-    bool simple = true;  // all starts of the chunk lie in the first window
-    __syncwarp();
-    for (;;) {
-        const bool inside = off >= cfirst && off <= cend;
-        if (inside) ws.starts[off - cfirst] = 0x80;
-        const unsigned m = __ballot_sync(kFull, inside);
-        // continue while the window's last entry still starts inside the chunk
-        if (!(m >> 31)) break;
-        simple = false;
-        base += 32;
-        idx = base + lane;
-        off = idx <= A.count ? A.offsets[idx] : LLONG_MAX;
-    }
-    __syncwarp();
-    uint32_t from_prev, from_next;
-    chunk_classes<U>(cb, unit_is_high(ch.halo), unit_is_low(ch.halo), lane, from_prev, from_next);
-    uint32_t nz[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int r0 = u * kWarpSliceUnits + lane * kUnitsPerVec;
-        const long long p0 = cfirst + r0;
-        const uint2 st = *reinterpret_cast<const uint2 *>(ws.starts + r0);  // starts at units r0 .. r0+7
-        const uint32_t st_next = ws.starts[r0 + 8] >> 7;                   // a start at unit r0+8
-        uint32_t bad_lo, bad_hi;
-        vec_bad<U>(cb, u, from_prev, from_next, st.x, st.y, st_next, bad_lo, bad_hi);
-        if (edge) {
-            uint32_t vlo, vhi;
-            bits_to_flags(batch_valid_bits8(p0, lo, hi), vlo, vhi);
-            bad_lo &= vlo;
-            bad_hi &= vhi;
-        }
-        const uint32_t vbad = bad_lo | bad_hi;
-        if constexpr (MODE == kModeOut) {
-            uint4 f = ch.v[u];
-            if (vbad) f = fix_vec(f, bad_lo, bad_hi);
-            batch_store_vec<MODE, ST>(dst + u * kWarpSliceUnits, f, edge, p0, lo, hi, 0u);
-        } else if constexpr (MODE == kModeInPlace || MODE == kModeInPlaceFirst) {
-            if (vbad)
-                batch_store_vec<MODE, ST>(dst + u * kWarpSliceUnits, fix_vec(ch.v[u], bad_lo, bad_hi), edge, p0, lo,
-                                          hi, gather4(bad_lo) | (gather4(bad_hi) << 4));
-        }
-        if constexpr (MODE == kModeInPlaceFirst) {
-            const uint32_t bits8 = gather4(bad_lo) | (gather4(bad_hi) << 4);
-            ws.bad[u * 32 + lane] = (uint8_t)bits8;
-            nz[u] = __ballot_sync(kFull, bits8 != 0);
-        }
-    }
-    if constexpr (MODE == kModeInPlaceFirst) {
-        uint32_t any = 0;
-#pragma unroll
-        for (int u = 0; u < U; ++u) any |= nz[u];
-        if (any == 0) return;
-        __syncwarp();
-        // Per-string first-error index, one lane per string: the string of
-        // window entry `lane` starts at `off` and ends at the next entry; its
-        // first mismatched unit in this chunk is the first set bit from its
-        // start.  Strings that start in this chunk take the window entries in
-        // [cfirst, cend); the string holding the chunk's first units (it
-        // started earlier) takes the units before the first of them.
-        const int q0 = first_mismatch_from<U>(ws, nz, 0);
-        const long long first_start = __shfl_sync(kFull, off_first, fs_lane);  // offsets[s_first]
-        const long long before = __shfl_sync(kFull, off_first, fs_lane >= 1 ? fs_lane - 1 : 0);
-        if (lane == 0 && s_first >= 1 && s_first <= A.count && q0 < (int)CU && cfirst + q0 < first_start) {
-            const long long start = fs_lane >= 1 ? before : A.offsets[s_first - 1];
-            atomicMin(&A.first_bad[s_first - 1], cfirst + q0 - start);
-        }
-        long long wbase = base_first;
-        long long woff = off_first;
-        for (;;) {
-            const long long wnext = __shfl_down_sync(kFull, woff, 1);
-            const long long widx = wbase + lane;
-            const bool starts_here = woff >= cfirst && woff < cend && widx < A.count;
-            if (starts_here) {
-                const long long end = lane < 31 ? wnext : A.offsets[widx + 1];
-                const int q = first_mismatch_from<U>(ws, nz, (int)(woff - cfirst));
-                if (cfirst + q < end && q < (int)CU) atomicMin(&A.first_bad[widx], cfirst + q - woff);
-            }
-            if (simple || !__shfl_sync(kFull, starts_here ? 1 : 0, 31)) break;
-            wbase += 32;
-            const long long ni = wbase + lane;
-            woff = ni <= A.count ? A.offsets[ni] : LLONG_MAX;
-        }
-    }
-}
-
-template <int MODE, int ST, int U, bool PF>
-__global__ void __launch_bounds__(kBlockThreads) batch_kernel(const BatchArgs A) {
-    __shared__ WarpScratch<U> s_scratch[kBlockThreads / 32];
-
-    const int lane = threadIdx.x & 31;
-    WarpScratch<U> &ws = s_scratch[threadIdx.x >> 5];
-    wait_prior_grids();
-
-    const long long lo = A.offsets[0];
-    const long long hi = A.offsets[A.count];
-    if (lo < 0 || hi <= lo) return;
-    const long long vbeg = (lo + A.a) >> 3;
-    const long long vend = (hi + A.a + 7) >> 3;
-    const long long chunks = (vend - vbeg + 32LL * U - 1) / (32LL * U);
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long c_begin = gwarp * chunks / nwarps;
-    const long long c_end = (gwarp + 1) * chunks / nwarps;
-    const uint4 *vin = reinterpret_cast<const uint4 *>(A.in - A.a);
-
-    long long hint = 0;
-    if constexpr (PF) {
-        BatchChunk<U> nv;
-        if (c_begin < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + c_begin * (32LL * U), lo, hi, lane, nv);
-        for (long long c = c_begin; c < c_end; ++c) {
-            const BatchChunk<U> v = nv;
-            if (c + 1 < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + (c + 1) * (32LL * U), lo, hi, lane, nv);
-            const long long cfirst = (vbeg + c * (32LL * U)) * 8 - A.a;
-            process_batch_chunk<MODE, ST, U>(A, cfirst, lo, hi, v, lane, ws, hint);
-        }
-    } else {
-        for (long long c = c_begin; c < c_end; ++c) {
-            const long long vfirst = vbeg + c * (32LL * U);
-            BatchChunk<U> v;
-            load_batch_chunk<MODE, U>(A, vin, vfirst, lo, hi, lane, v);
-            process_batch_chunk<MODE, ST, U>(A, vfirst * 8 - A.a, lo, hi, v, lane, ws, hint);
-        }
-    }
-    allow_next_grid();
-}
-
 // ---------------------------------------------------------------------------
-// Per-string first-error index (the check), word-lane form.
+// Per chunk, on bit words.
 //
 // After classification each lane packs, per vector, the surrogate bits and
 // the low-surrogate bits of its 8 units (bit k = unit k) into one 16-bit
 // entry of a per-warp table.  Read back four entries at a time, the table
 // gives lane l the units [1024 j + 32 l, +32) of the chunk as 32-bit words,
 // one per 1024 units of chunk (j = 0 for U = 4, j = 0, 1 for U = 8): H (high
-// surrogates) and L (low surrogates).  The 2048-unit chunk halves the
-// per-chunk cost of the offsets window and the lookups per unit (1M strings:
-// 50 -> 43 us).  The string starts inside the
-// chunk become a third word S (one shared atomic OR per start, from a window
-// of the offsets).  The Section 1 rule with every string end as a boundary
-// (Section 3.1) is then word logic in each lane:
-//   Hprev  = H one unit up (bit W-1 of the lane before; lane 0: the unit
+// surrogates) and L (low surrogates).  A chunk without any surrogate is done
+// at once (out of place it is copied).  The string starts inside the chunk
+// become a third word S (one shared atomic OR per start, from a window of the
+// offsets).  The Section 1 rule with every string end as a boundary (Section
+// 3.1) is then word logic in each lane:
+//   Hprev  = H one unit up (bit 31 of the lane before; lane 0: the unit
 //            before the chunk),  Lnext = L one unit down;
 //   a unit that starts a string has no left neighbour, the unit before it no
 //   right neighbour:  NoRight = S one unit down;
 //   bad    = H & ~(Lnext & ~NoRight) | L & ~(Hprev & ~S).
-// Each lane of the offsets window then takes one string that meets the chunk
-// and finds its first bad unit from max(start, chunk start) in constant time:
-// the word holding that unit (one shuffle), else the first later word with a
-// bad unit (a ballot summary and one more shuffle).  Results go to first_bad
-// with atomicMin, over the string lengths a small kernel writes first.
+// Then, by form:
+//   - out of place: each lane takes its vectors' 8 bits from the lane word
+//     that holds them (one shuffle per vector), replaces in registers and
+//     stores each vector once;
+//   - in place: one 2-byte store of U+FFFD per bad unit, or for a dense chunk
+//     the bad words back through shared memory to one byte per vector and a
+//     16-byte block per vector that holds one (no ordering between warps is
+//     needed: a replacement never changes a neighbour's verdict);
+//   - per-string first-error index: each lane of the offsets window takes one
+//     string that meets the chunk and finds its first bad unit from
+//     max(start, chunk start) in constant time: the word holding that unit
+//     (one shuffle), else the first later word with a bad unit (a ballot
+//     summary and one more shuffle).  Results go to first_bad with an atomic
+//     minimum, over the string lengths a small kernel writes first.
+// The 2048-unit chunk halves the per-unit cost of the offsets window and the
+// lookups (1M strings, check: 50 -> 43 us).
 
-// Per-warp table and start words of the word-lane check.
+// Per-warp table, start words and dense-store bytes of the word kernels.
 template <int U>
 struct __align__(16) WordScratch {
     uint16_t cls[U * 32];      // vector v of the chunk: bit k = unit k is a surrogate, bit 8+k = it is a low one
     uint32_t starts[U * 8];    // word w: bit j set when a string starts at unit 32 w + j of the chunk
+    uint32_t bad[U * 8];       // repair of a dense chunk: the bad words again (byte v = vector v's 8 bits)
 };
+
+// Vector u of this lane of the chunk at vector vfirst, read again for the
+// dense store path (unit loads at the batch's ends, 0 outside [lo, hi)).
+__device__ __forceinline__ uint4 reload_batch_vec(const BatchArgs &A, const uint4 *vin, long long vfirst, int u,
+                                                  long long lo, long long hi, int lane, bool edge) {
+    if (!edge) return ld_plain(vin + vfirst + 32 * u + lane);
+    const long long p0 = (vfirst + 32 * u + lane) * 8 - A.a;
+    uint4 v = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (p0 + k >= lo && p0 + k < hi) vec_set_unit(v, k, A.in[p0 + k]);
+    return v;
+}
+
+// Above this many replaced units in one lane word (any lane of the warp) a
+// repair chunk stores whole 16-byte blocks instead of single units.
+constexpr int kSparseMax = 4;
 
 // The strings base .. base+31 of the batch, one per lane: its start and end
 // (kFar for lanes past the last string).  kFar stays far from overflow when
@@ -401,12 +213,19 @@ struct CheckState {
     bool waited = false;
 };
 
-template <int U>
-__device__ __forceinline__ void check_words_chunk(const BatchArgs &A, long long cfirst, const BatchChunk<U> &ch,
-                                                  int lane, WordScratch<U> &ws, CheckState &st) {
+template <int MODE, int ST, int U>
+__device__ __forceinline__ void words_chunk(const BatchArgs &A, const uint4 *vin, long long vfirst, long long lo,
+                                            long long hi, const BatchChunk<U> &ch, int lane, WordScratch<U> &ws,
+                                            CheckState &st) {
     constexpr int NW = U / 4;            // 32-unit words per lane
     constexpr int CU = U * kWarpSliceUnits;
+    constexpr bool kOut = MODE == kModeOut;
+    constexpr bool kRepair = MODE != kModeCheck;
+    constexpr bool kLookup = MODE == kModeCheck || MODE == kModeInPlaceFirst;
     static_assert(NW == 1 || NW == 2, "chunk width");
+    const long long cfirst = vfirst * 8 - A.a;
+    const bool edge = (cfirst < lo) || (cfirst + CU > hi);
+    const long long lfirst = cfirst + lane * kUnitsPerVec;
 
     // Classification (high byte only, Section 3.3), packed to the table one
     // vector at a time so that its registers free at once, and the fast
@@ -425,6 +244,12 @@ __device__ __forceinline__ void check_words_chunk(const BatchArgs &A, long long 
         ws.cls[32 * u + lane] = (uint16_t)prmt(s8, l8, 0x0073);
     }
     if (!__any_sync(kFull, acc != 0)) {  // no surrogate: nothing in the chunk is mismatched
+        if constexpr (kOut) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                batch_store_vec<kModeOut, ST>(A.out + lfirst + u * kWarpSliceUnits, ch.v[u], edge,
+                                              lfirst + u * kWarpSliceUnits, lo, hi, 0u);
+        }
         if (st.have_nw) st.hint = st.nw.base;  // the window was for this chunk
         st.have_nw = false;
         return;
@@ -513,57 +338,118 @@ __device__ __forceinline__ void check_words_chunk(const BatchArgs &A, long long 
     // Summary: bit w set when word w (lane w & 31, word w >> 5) has a bad unit.
     unsigned long long nz = __ballot_sync(kFull, bad[0] != 0);
     if constexpr (NW == 2) nz |= (unsigned long long)__ballot_sync(kFull, bad[1] != 0) << 32;
+    if constexpr (kOut) {
+        // Out of place: each vector's 8 bits from the lane word that holds
+        // them (vector 32u + lane is byte lane & 3 of word 8u + lane / 4),
+        // replaced in registers, stored once.
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t wsrc = __shfl_sync(kFull, bad[u >> 2], 8 * (u & 3) + (lane >> 2));
+            const uint32_t bits8 = (wsrc >> (8 * (lane & 3))) & 0xFFu;
+            uint4 f = ch.v[u];
+            if (bits8) {
+                uint32_t flo, fhi;
+                bits_to_flags(bits8, flo, fhi);
+                f = fix_vec(f, flo, fhi);
+            }
+            batch_store_vec<kModeOut, ST>(A.out + lfirst + u * kWarpSliceUnits, f, edge, lfirst + u * kWarpSliceUnits,
+                                          lo, hi, 0u);
+        }
+        return;
+    }
     if (nz == 0) return;
 
-    // first_bad holds the lengths once the grid before this one is done.
-    if (!st.waited) {
-        wait_prior_grids();
-        st.waited = true;
+    if constexpr (kRepair) {
+        // Replacements: one 2-byte store per bad unit, or for a dense chunk
+        // the bad bits back to one byte per vector (the byte order of the
+        // words makes byte v of ws.bad vector v's 8 bits) and a 16-byte block
+        // per vector holding one.  Units outside [lo, hi) are never bad.
+        int pop = 0;
+#pragma unroll
+        for (int j = 0; j < NW; ++j) pop += __popc(bad[j]);
+        if (__reduce_max_sync(kFull, (unsigned)pop) <= (unsigned)kSparseMax) {
+            if constexpr (kOut) __syncwarp();  // this chunk's copies (other lanes' too) before the replacements
+#pragma unroll
+            for (int j = 0; j < NW; ++j) {
+                uint16_t *base = A.out + cfirst + 1024 * j + 32 * lane;
+                uint32_t rest = bad[j];
+                while (rest) {
+                    base[__ffs(rest) - 1] = (uint16_t)0xFFFDu;
+                    rest &= rest - 1;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NW; ++j) ws.bad[32 * j + lane] = bad[j];
+            __syncwarp();
+            const uint8_t *bytes = reinterpret_cast<const uint8_t *>(ws.bad);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t bits8 = bytes[32 * u + lane];
+                if (bits8) {
+                    uint32_t flo, fhi;
+                    bits_to_flags(bits8, flo, fhi);
+                    const uint4 v = reload_batch_vec(A, vin, vfirst, u, lo, hi, lane, edge);
+                    batch_store_vec<MODE, ST>(A.out + lfirst + u * kWarpSliceUnits, fix_vec(v, flo, fhi), edge,
+                                              lfirst + u * kWarpSliceUnits, lo, hi, bits8);
+                }
+            }
+        }
     }
-    // Each lane's string: its first bad unit from max(start, cfirst) within
-    // the chunk, if that lies before the string's end.
-    Window m = w;
-    int mS = relS, mE = relE;
-    for (int k = 0;;) {
-        const unsigned r = mS > 0 ? (unsigned)mS : 0u;
-        const unsigned wi = (r >> 5) & (32 * NW - 1);  // lanes that take nothing read any word
-        uint32_t b1 = __shfl_sync(kFull, bad[0], wi & 31u);
-        if constexpr (NW == 2) {
-            const uint32_t x = __shfl_sync(kFull, bad[1], wi & 31u);
-            b1 = (wi >> 5) ? x : b1;
+    if constexpr (kLookup) {
+        // first_bad holds the lengths once the grid before this one is done.
+        if (!st.waited) {
+            wait_prior_grids();
+            st.waited = true;
         }
-        b1 &= 0xFFFFFFFFu << (r & 31);
-        const unsigned long long later = wi < 32 * NW - 1 ? nz & (~0ull << (wi + 1)) : 0ull;
-        const unsigned w2 = later ? (unsigned)(__ffsll((long long)later) - 1) : 0u;
-        uint32_t b2 = __shfl_sync(kFull, bad[0], w2 & 31u);
-        if constexpr (NW == 2) {
-            const uint32_t x = __shfl_sync(kFull, bad[1], w2 & 31u);
-            b2 = (w2 >> 5) ? x : b2;
+        // Each lane's string: its first bad unit from max(start, cfirst) within
+        // the chunk, if that lies before the string's end.
+        Window m = w;
+        int mS = relS, mE = relE;
+        for (int k = 0;;) {
+            const unsigned r = mS > 0 ? (unsigned)mS : 0u;
+            const unsigned wi = (r >> 5) & (32 * NW - 1);  // lanes that take nothing read any word
+            uint32_t b1 = __shfl_sync(kFull, bad[0], wi & 31u);
+            if constexpr (NW == 2) {
+                const uint32_t x = __shfl_sync(kFull, bad[1], wi & 31u);
+                b1 = (wi >> 5) ? x : b1;
+            }
+            b1 &= 0xFFFFFFFFu << (r & 31);
+            const unsigned long long later = wi < 32 * NW - 1 ? nz & (~0ull << (wi + 1)) : 0ull;
+            const unsigned w2 = later ? (unsigned)(__ffsll((long long)later) - 1) : 0u;
+            uint32_t b2 = __shfl_sync(kFull, bad[0], w2 & 31u);
+            if constexpr (NW == 2) {
+                const uint32_t x = __shfl_sync(kFull, bad[1], w2 & 31u);
+                b2 = (w2 >> 5) ? x : b2;
+            }
+            const int q = b1 ? (int)(wi << 5) + __ffs(b1) - 1 : later ? (int)(w2 << 5) + __ffs(b2) - 1 : CU + 2;
+            // (The index is never negative: the unsigned minimum is the same, and
+            // a native reduction.)
+            if (mS < CU && q < mE)
+                atomicMin(reinterpret_cast<unsigned long long *>(&A.first_bad[m.base + lane]),
+                          (unsigned long long)((long long)q - (m.start - cfirst)));
+            if (++k >= nwin) break;
+            load_window(A, m.base + 32, lane, m);
+            mS = rel_pos<CU>(m.start, cfirst);
+            mE = rel_pos<CU>(m.end, cfirst);
         }
-        const int q = b1 ? (int)(wi << 5) + __ffs(b1) - 1 : later ? (int)(w2 << 5) + __ffs(b2) - 1 : CU + 2;
-        // (The index is never negative: the unsigned minimum is the same, and
-        // a native reduction.)
-        if (mS < CU && q < mE)
-            atomicMin(reinterpret_cast<unsigned long long *>(&A.first_bad[m.base + lane]),
-                      (unsigned long long)((long long)q - (m.start - cfirst)));
-        if (++k >= nwin) break;
-        load_window(A, m.base + 32, lane, m);
-        mS = rel_pos<CU>(m.start, cfirst);
-        mE = rel_pos<CU>(m.end, cfirst);
     }
 }
 
-// At least 4 resident blocks per SM: without the bound the 2048-unit form takes
-// 79 registers and 3 blocks; with it 63 and no spills.
-template <int U, bool PF>
-__global__ void __launch_bounds__(kBlockThreads, 4) batch_check_kernel(const BatchArgs A) {
+// At least 4 resident blocks per SM: without the bound the 2048-unit check
+// takes 79 registers and 3 blocks; with it 63 and no spills.
+template <int MODE, int ST, int U, bool PF>
+__global__ void __launch_bounds__(kBlockThreads, 4) batch_words_kernel(const BatchArgs A) {
+    constexpr bool kLookup = MODE == kModeCheck || MODE == kModeInPlaceFirst;
     __shared__ WordScratch<U> s_scratch[kBlockThreads / 32];
     const int lane = threadIdx.x & 31;
     WordScratch<U> &ws = s_scratch[threadIdx.x >> 5];
-    // No wait for the grid before this one here: it is the lengths kernel,
-    // which writes only first_bad and lets this grid start once it has waited
-    // for its own predecessors, so `in` and `offsets` are final.  The wait
-    // comes before the first atomic on first_bad, and before the exit.
+    // With per-string results the grid before this one is the lengths
+    // kernel, which writes only first_bad and lets this grid start once it
+    // has waited for its own predecessors, so `in` and `offsets` are final:
+    // the wait comes before the first atomic on first_bad (and before the
+    // exit).  The repairs wait here.
+    if constexpr (!kLookup) wait_prior_grids();
     const long long lo = A.offsets[0];
     const long long hi = A.offsets[A.count];
     if (lo >= 0 && hi > lo) {
@@ -578,23 +464,23 @@ __global__ void __launch_bounds__(kBlockThreads, 4) batch_check_kernel(const Bat
         CheckState st;
         if constexpr (PF) {
             BatchChunk<U> nv;
-            if (c_begin < c_end) load_batch_chunk<kModeCheck, U>(A, vin, vbeg + c_begin * (32LL * U), lo, hi, lane, nv);
+            if (c_begin < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + c_begin * (32LL * U), lo, hi, lane, nv);
             for (long long c = c_begin; c < c_end; ++c) {
                 const BatchChunk<U> v = nv;
-                if (c + 1 < c_end) load_batch_chunk<kModeCheck, U>(A, vin, vbeg + (c + 1) * (32LL * U), lo, hi, lane, nv);
-                check_words_chunk<U>(A, (vbeg + c * (32LL * U)) * 8 - A.a, v, lane, ws, st);
+                if (c + 1 < c_end) load_batch_chunk<MODE, U>(A, vin, vbeg + (c + 1) * (32LL * U), lo, hi, lane, nv);
+                words_chunk<MODE, ST, U>(A, vin, vbeg + c * (32LL * U), lo, hi, v, lane, ws, st);
             }
         } else {
             for (long long c = c_begin; c < c_end; ++c) {
                 const long long vfirst = vbeg + c * (32LL * U);
                 BatchChunk<U> v;
-                load_batch_chunk<kModeCheck, U>(A, vin, vfirst, lo, hi, lane, v);
-                check_words_chunk<U>(A, vfirst * 8 - A.a, v, lane, ws, st);
+                load_batch_chunk<MODE, U>(A, vin, vfirst, lo, hi, lane, v);
+                words_chunk<MODE, ST, U>(A, vin, vfirst, lo, hi, v, lane, ws, st);
             }
         }
     }
     allow_next_grid();
-    wait_prior_grids();
+    if constexpr (kLookup) wait_prior_grids();
 }
 
 // first_bad[s] = length of string s (the value for a well-formed string).
@@ -610,27 +496,28 @@ __global__ void batch_lengths_kernel(const long long *offsets, long long count, 
 }
 
 template <int MODE, int ST>
-static const void *batch_ptr(int u, bool pf) {
-    if (pf) return u == 2 ? (const void *)batch_kernel<MODE, ST, 2, true> : (const void *)batch_kernel<MODE, ST, 4, true>;
-    return u == 2 ? (const void *)batch_kernel<MODE, ST, 2, false> : (const void *)batch_kernel<MODE, ST, 4, false>;
+static const void *words_ptr(int u, bool pf) {
+    if (pf)
+        return u == 2 ? (const void *)batch_words_kernel<MODE, ST, 4, true>
+                      : (const void *)batch_words_kernel<MODE, ST, 8, true>;
+    return u == 2 ? (const void *)batch_words_kernel<MODE, ST, 4, false>
+                  : (const void *)batch_words_kernel<MODE, ST, 8, false>;
 }
 
-// The check's chunk: one 32-unit word per lane (1024 units) for the narrow
-// setting, two (2048 units) for the wide one.
-static const void *check_words_ptr(int u, bool pf) {
-    if (pf) return u == 2 ? (const void *)batch_check_kernel<4, true> : (const void *)batch_check_kernel<8, true>;
-    return u == 2 ? (const void *)batch_check_kernel<4, false> : (const void *)batch_check_kernel<8, false>;
-}
+// Chunk width of each mode when the configuration leaves it open (0):
+// 1024 units out of place (1M strings: 69.5 against 72.8 us), 2048 for the
+// rest (in place 66 against 69 us, check 43 against 50 us).
+static int batch_u(int mode, int u) { return u == 2 || u == 4 ? u : mode == kModeOut ? 2 : 4; }
 
 static const void *pick_batch(int mode, int st, int u, bool pf) {
-    if (mode == kModeCheck) return check_words_ptr(u, pf);
-    if (mode == kModeInPlaceFirst) return batch_ptr<kModeInPlaceFirst, 16>(u, pf);
-    if (mode == kModeInPlace) return batch_ptr<kModeInPlace, 16>(u, pf);
+    if (mode == kModeCheck) return words_ptr<kModeCheck, 16>(u, pf);
+    if (mode == kModeInPlaceFirst) return words_ptr<kModeInPlaceFirst, 16>(u, pf);
+    if (mode == kModeInPlace) return words_ptr<kModeInPlace, 16>(u, pf);
     switch (st) {
-        case 16: return batch_ptr<kModeOut, 16>(u, pf);
-        case 8: return batch_ptr<kModeOut, 8>(u, pf);
-        case 4: return batch_ptr<kModeOut, 4>(u, pf);
-        default: return batch_ptr<kModeOut, 2>(u, pf);
+        case 16: return words_ptr<kModeOut, 16>(u, pf);
+        case 8: return words_ptr<kModeOut, 8>(u, pf);
+        case 4: return words_ptr<kModeOut, 4>(u, pf);
+        default: return words_ptr<kModeOut, 2>(u, pf);
     }
 }
 
@@ -659,19 +546,20 @@ cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream) {
                                       largs, 0, stream);
         if (e != cudaSuccess) return e;
     }
-    const void *fn = pick_batch(L.mode, st, L.units_per_thread == 2 ? 2 : 4, L.prefetch);
+    const int u = batch_u(L.mode, L.units_per_thread);
+    const void *fn = pick_batch(L.mode, st, u, L.prefetch);
     void *args[] = {(void *)&A};
     const long long warps = (long long)L.blocks * (kBlockThreads / 32);
-    const long long chunk_units = (L.units_per_thread == 2 ? 2 : 4) * (long long)kWarpSliceUnits;
-    // The word-lane check overlaps the lengths kernel before it (it waits only
-    // before its first atomic), which needs the attribute.
-    const bool pdl = L.mode == kModeCheck || L.full_occupancy ||
+    const long long chunk_units = u == 2 ? 1024 : 2048;
+    // The per-string forms overlap the lengths kernel before them (they wait
+    // only before their first atomic), which needs the attribute.
+    const bool pdl = L.mode == kModeCheck || L.mode == kModeInPlaceFirst || L.full_occupancy ||
                      (L.units_hint > 0 && pdl_fits((L.units_hint / chunk_units + warps) / warps, false));
     return launch_kernel(fn, dim3((unsigned)L.blocks), dim3(kBlockThreads), args, 0, stream, pdl);
 }
 
 const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch) {
-    return pick_batch(mode, 16, u == 2 ? 2 : 4, prefetch);
+    return pick_batch(mode, 16, batch_u(mode, u), prefetch);
 }
 
 // ---------------------------------------------------------------------------

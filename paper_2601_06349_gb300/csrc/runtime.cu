@@ -87,7 +87,7 @@ static bool config_valid(const utf16_config &c) {
            (c.inplace_unit_stores == 0 || c.inplace_unit_stores == 1) &&
            (c.single_units_per_thread == 0 || c.single_units_per_thread == 2 || c.single_units_per_thread == 4) &&
            c.single_blocks_per_sm >= 0 &&
-           c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
+           c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 0 || c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
            (c.batch_prefetch == 0 || c.batch_prefetch == 1) && c.batch_blocks_per_sm >= 0 &&
            c.batch_blocks_per_sm <= 64;
 }
@@ -135,8 +135,11 @@ int get_ctx(DeviceCtx **out) {
     d.single_variant = env_int("UTF16WF_SINGLE_VARIANT", kVariantLdg);
     d.single_units_per_thread = env_int("UTF16WF_SINGLE_U", 0);
     d.single_blocks_per_sm = env_int("UTF16WF_SINGLE_BLOCKS_PER_SM", 0);
-    d.batch_units_per_thread = env_int("UTF16WF_BATCH_U", 4);
-    d.batch_prefetch = env_int("UTF16WF_BATCH_PREFETCH", 1);
+    // Batches: the chunk width of each mode (0; 1024 units out of place,
+    // 2048 otherwise) and no next chunk in flight, which only cost registers
+    // (1M strings out of place: 69.5 against 77 us).
+    d.batch_units_per_thread = env_int("UTF16WF_BATCH_U", 0);
+    d.batch_prefetch = env_int("UTF16WF_BATCH_PREFETCH", 0);
     d.batch_blocks_per_sm = env_int("UTF16WF_BATCH_BLOCKS_PER_SM", 0);
     d.check_variant = env_int("UTF16WF_CHECK_VARIANT", kVariantLdg);
     d.inplace_unit_stores = env_int("UTF16WF_INPLACE_UNIT_STORES", 0);
@@ -147,15 +150,15 @@ int get_ctx(DeviceCtx **out) {
     d.inplace_variant = env_int("UTF16WF_INPLACE_VARIANT", kVariantLdgPrefetch);
     d.check_blocks_per_sm = env_int("UTF16WF_CHECK_BLOCKS_PER_SM", 0);
     d.inplace_blocks_per_sm = env_int("UTF16WF_INPLACE_BLOCKS_PER_SM", 0);
-    // The batch check runs faster without the next chunk in flight (77.5 vs
-    // 84-87 us on 1,000,000 strings), the batch repair faster with it (70 vs 75).
+    // The batch check runs faster without the next chunk in flight (1M
+    // strings: 43 against 64 us).
     d.batch_check_prefetch = env_int("UTF16WF_BATCH_CHECK_PREFETCH", 0);
     // Programmatic dependent launch: back-to-back small calls measured 7-11 %
     // faster (1024 units 3.12 -> 2.89 us, 1,000,000 units 5.21 -> 4.68 us),
     // long ones unchanged.
     g_pdl = env_int("UTF16WF_PDL", 1) != 0;
     if (!config_valid(d))
-        d = utf16_config{kVariantLdg, 4, 0, 4, 1, 0, kVariantLdg, 0, kVariantLdgPrefetch, 0, 0, 0};
+        d = utf16_config{kVariantLdg, 0, 0, 0, 0, 0, kVariantLdg, 0, kVariantLdgPrefetch, 0, 0, 0};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);

@@ -16,7 +16,7 @@ from gpu_util import Guarded, first_diff, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 SINGLE = [(0, 4, 0), (0, 2, 0), (1, 4, 0), (1, 2, 0), (2, 4, 0), (2, 4, 1), (0, 4, 1), (1, 2, 2)]
-BATCH = [(4, 0, 0), (2, 0, 0), (4, 1, 0), (2, 1, 0), (4, 0, 1)]
+BATCH = [(0, 0, 0), (4, 0, 0), (2, 0, 0), (4, 1, 0), (2, 1, 0), (4, 0, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -146,7 +146,7 @@ def test_autotuner_choice_is_correct(pkg):
     du = to_dev(units)
     do = torch.from_numpy(offs).cuda()
     bcfg = pkg.autotune_batch(du, do, reps=3)
-    assert bcfg.batch_units_per_thread in (2, 4)
+    assert bcfg.batch_units_per_thread in (0, 2, 4)
     got = to_host(pkg.to_well_formed_batch(du, do))
     assert np.array_equal(got, oracle.to_well_formed_batch(units, offs))
     pkg.check_device_errors()
