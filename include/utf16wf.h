@@ -351,6 +351,13 @@ typedef struct {
     int direct_host_access;       /* 1: a small request whose host buffers are pinned (page-locked, mapped) is
                                      copied in and out by the GPU itself, in 8 KiB pieces (no CPU copies; each
                                      submit then queries the buffers' attributes); 0 (default): staged */
+    int64_t inject_copy_fail_mod; /* testing: 0 = off; k > 0 = a copy step of every k-th launched batch (launch
+                                     number % k == k - 1) fails: the copies are not issued, the batch's later work
+                                     neither, and its requests complete with UTF16_ECUDA (host-side fault injection,
+                                     nothing faults on the GPU) */
+    int inject_copy_fail_step;    /* the failing step: 0 = the host-to-device copies (no output is touched), 1 = the
+                                     device-to-host copies (outputs the engine copies back stay untouched; requests
+                                     the GPU writes itself -- host passes, direct access -- may hold their result) */
 } utf16_server_options;
 
 typedef struct {

@@ -52,7 +52,8 @@ class ServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_batch_strings", ctypes.c_int64),
                 ("max_batch_bytes", ctypes.c_int64), ("max_inflight_batches", ctypes.c_int),
                 ("staging_bytes", ctypes.c_int64), ("small_request_bytes", ctypes.c_int64),
-                ("inject_fail_mod", ctypes.c_int64), ("direct_host_access", ctypes.c_int)]
+                ("inject_fail_mod", ctypes.c_int64), ("direct_host_access", ctypes.c_int),
+                ("inject_copy_fail_mod", ctypes.c_int64), ("inject_copy_fail_step", ctypes.c_int)]
 
 
 class Completion(ctypes.Structure):

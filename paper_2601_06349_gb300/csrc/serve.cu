@@ -424,8 +424,15 @@ static void launch_batch_slot(utf16_server *S, int si) {
         return;
     }
 
-    cudaError_t e = cudaMemcpyAsync(b.d_offsets, h_off, (size_t)(strings + 1) * sizeof(int64_t),
-                                    cudaMemcpyHostToDevice, b.stream);
+    // Host-side fault injection of a copy step (testing): the step's copies
+    // are not issued and the batch fails as if they had.
+    const int64_t fail_mod = S->opt.inject_copy_fail_mod;
+    const bool fail_copy = fail_mod > 0 && (int64_t)(b.seq % (uint64_t)fail_mod) == fail_mod - 1;
+    const cudaError_t kInjected = cudaErrorUnknown;
+    cudaError_t e = (fail_copy && S->opt.inject_copy_fail_step == 0)
+                        ? kInjected
+                        : cudaMemcpyAsync(b.d_offsets, h_off, (size_t)(strings + 1) * sizeof(int64_t),
+                                          cudaMemcpyHostToDevice, b.stream);
     if (e == cudaSuccess && nd)
         e = cudaMemcpyAsync(b.d_desc, h_desc, (size_t)nd * sizeof(CopyDesc), cudaMemcpyHostToDevice, b.stream);
     if (e == cudaSuccess && b.small_units)
@@ -458,6 +465,7 @@ static void launch_batch_slot(utf16_server *S, int si) {
     // strings' first-error slots, one fused pass each fills the slot.
     for (const Request &r : b.reqs)
         if (e == cudaSuccess && r.host_pass) e = launch_host_pass(S, b, r);
+    if (e == cudaSuccess && fail_copy && S->opt.inject_copy_fail_step == 1) e = kInjected;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h_first, b.d_first, (size_t)strings * sizeof(int64_t), cudaMemcpyDeviceToHost, b.stream);
     if (e == cudaSuccess && b.small_units)
@@ -467,6 +475,11 @@ static void launch_batch_slot(utf16_server *S, int si) {
             e = cudaMemcpyAsync(r.out, b.d_units + r.dev_off, (size_t)r.n * 2u, cudaMemcpyDeviceToHost, b.stream);
     if (e == cudaSuccess) e = cudaEventRecord(b.ev_done, b.stream);
     if (e != cudaSuccess) {
+        cudaGetLastError();
+        // Work of this batch already on its stream may still use the slot's
+        // staging and arena space, which the completer hands on at once: wait
+        // for it first.
+        cudaStreamSynchronize(b.stream);
         cudaGetLastError();
         b.status = UTF16_ECUDA;
     }
@@ -667,6 +680,8 @@ int utf16_server_default_options(utf16_server_options *o) {
     o->small_request_bytes = 256LL << 10;
     o->inject_fail_mod = 0;
     o->direct_host_access = 0;
+    o->inject_copy_fail_mod = 0;
+    o->inject_copy_fail_step = 0;
     return UTF16_OK;
 }
 
@@ -675,7 +690,8 @@ int utf16_server_create(const utf16_server_options *opt, utf16_server **out) {
     const utf16_server_options &o = *opt;
     if (o.hbm_budget_bytes < (1 << 20) || o.max_batch_strings < 2 || o.max_batch_bytes < 1024 ||
         o.max_inflight_batches < 1 || o.max_inflight_batches > 64 || o.staging_bytes < 4096 ||
-        o.small_request_bytes < 0 || o.inject_fail_mod < 0 || o.direct_host_access < 0 || o.direct_host_access > 1)
+        o.small_request_bytes < 0 || o.inject_fail_mod < 0 || o.direct_host_access < 0 || o.direct_host_access > 1 ||
+        o.inject_copy_fail_mod < 0 || o.inject_copy_fail_step < 0 || o.inject_copy_fail_step > 1)
         return UTF16_EINVAL;
     std::unique_ptr<utf16_server> S(new utf16_server());
     S->opt = o;

@@ -137,7 +137,8 @@ def test_server_default_options_match_the_header(capi):
     o = pkg.ServerOptions()
     assert capi.utf16_server_default_options(ctypes.byref(o)) == 0
     assert (o.hbm_budget_bytes, o.max_batch_strings, o.max_batch_bytes, o.max_inflight_batches,
-            o.staging_bytes, o.small_request_bytes, o.inject_fail_mod, o.direct_host_access) == \
-        (4 << 30, 1 << 16, 16 << 20, 8, 32 << 20, 256 << 10, 0, 0)
+            o.staging_bytes, o.small_request_bytes, o.inject_fail_mod, o.direct_host_access,
+            o.inject_copy_fail_mod, o.inject_copy_fail_step) == \
+        (4 << 30, 1 << 16, 16 << 20, 8, 32 << 20, 256 << 10, 0, 0, 0, 0)
     text = open(os.path.join(HEADER_DIR, "utf16wf.h")).read()
     assert "16 MiB packed per batch, 8 slots, 32 MiB staging" in text

@@ -206,6 +206,41 @@ def test_injected_admission_failures_leave_others_exact(pkg):
     assert failed > 10
 
 
+@pytest.mark.parametrize("step", [0, 1])
+def test_injected_copy_failures_leave_others_exact(pkg, step):
+    """A copy step that fails (injected on the host in every third launched
+    batch: its host-to-device copies for step 0, its device-to-host copies
+    for step 1) completes that batch's requests with UTF16_ECUDA and leaves
+    their outputs untouched (these small requests are staged, and the engine
+    copies staged results back only on success).  Every other request is
+    exact, and the engine goes on serving the batches after a failed one."""
+    reqs = _requests(300, 16 + step, big=False)
+    want = _expect(reqs)
+    outs = [np.full_like(u, 0x5A5A) for u in reqs]
+    with pkg.Server(inject_copy_fail_mod=3, inject_copy_fail_step=step, max_batch_strings=16,
+                    max_inflight_batches=2) as srv:
+        tickets = [srv.submit(u, o) for u, o in zip(reqs, outs)]
+        res = {}
+        while len(res) < len(reqs):
+            c = srv.next(timeout_us=30_000_000)
+            assert c is not None
+            res[c["ticket"]] = c
+        st = srv.stats()
+    failed = ok = 0
+    for i, t in enumerate(tickets):
+        c = res[t]
+        if c["status"] == pkg.ECUDA:
+            assert np.all(outs[i] == 0x5A5A), i  # untouched
+            failed += 1
+        else:
+            assert c["status"] == 0 and c["first_bad"] == want[i][1], i
+            assert np.array_equal(outs[i], want[i][0]), i
+            ok += 1
+    assert st["batches"] >= 19  # at most 8 requests (16 strings) per batch
+    assert failed > 0 and ok > failed
+    pkg.check_device_errors()
+
+
 def test_cancel_before_admission(pkg):
     reqs = _requests(400, 15, big=False)
     want = _expect(reqs)
