@@ -420,8 +420,7 @@ def main():
         "config": workload_config(n),
         "execution": f"{world} independent GPU replicas" if world > 1 else "single GPU",
         "roofline": roofline,
-        "launch_config": {("default" if args.no_autotune else "autotuned"): tuned.as_dict(), "block_threads": 256,
-                          "vector_bytes": 16},
+        "launch_config": {("default" if args.no_autotune else "autotuned"): tuned.as_dict()},
         "gpu_launches": args.steps,
         "clocks": clk,
     }

@@ -242,6 +242,11 @@ typedef struct {
     int check_blocks_per_sm;     /* read-only check: persistent grid = SMs x this; 0 = as many as fit */
     int inplace_blocks_per_sm;   /* in-place repair of single strings: the same */
     int batch_check_prefetch;    /* per-string check of batches (utf16_is_well_formed_batch): 0 or 1 */
+    int block_threads;           /* threads per block: 128, 256 or 512; 0 (default) = 256 for single strings,
+                                    512 for batches.  The TMA data path always uses 256 */
+    int vector_bytes;            /* bytes each lane loads at once in the batch kernels: 8, 16 or 32 (256-bit
+                                    loads); 0 (default) = 32 for in-place batch repair, 16 for the other batch
+                                    forms.  Single strings use 16 */
 } utf16_config;
 
 /* Default configuration of the current device (used where nothing is tuned). */

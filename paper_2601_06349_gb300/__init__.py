@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
                 ("batch_prefetch", ctypes.c_int), ("batch_blocks_per_sm", ctypes.c_int),
                 ("check_variant", ctypes.c_int), ("inplace_unit_stores", ctypes.c_int),
                 ("inplace_variant", ctypes.c_int), ("check_blocks_per_sm", ctypes.c_int),
-                ("inplace_blocks_per_sm", ctypes.c_int), ("batch_check_prefetch", ctypes.c_int)]
+                ("inplace_blocks_per_sm", ctypes.c_int), ("batch_check_prefetch", ctypes.c_int),
+                ("block_threads", ctypes.c_int), ("vector_bytes", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -72,10 +72,10 @@ void log_candidate(const char *what, const utf16_config &c, float ms) {
     if (!tune_log()) return;
     fprintf(stderr,
             "utf16wf tune %s: single v%d U%d bps%d | check v%d bps%d | inplace v%d bps%d | batch U%d pf%d bps%d "
-            "check-pf%d: %.4f ms\n",
+            "check-pf%d | threads %d vector %d: %.4f ms\n",
             what, c.single_variant, c.single_units_per_thread, c.single_blocks_per_sm, c.check_variant,
             c.check_blocks_per_sm, c.inplace_variant, c.inplace_blocks_per_sm, c.batch_units_per_thread,
-            c.batch_prefetch, c.batch_blocks_per_sm, c.batch_check_prefetch, ms);
+            c.batch_prefetch, c.batch_blocks_per_sm, c.batch_check_prefetch, c.block_threads, c.vector_bytes, ms);
 }
 
 // Fastest of three trials of `reps` back-to-back launches (ms per trial):
@@ -128,14 +128,16 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
     utf16_config base = ctx->def, winner = base;
     float best_ms = 1e30f;
     for (int variant = 0; variant <= 2; ++variant) {
-        for (int u : {2, 4}) {
-            if (variant == kVariantTma && u != 4) continue;
+        for (int u : {2, 4})
+        for (int bt : {128, 256, 512}) {
+            if (variant == kVariantTma && (u != 4 || bt != kBlockThreads)) continue;
             utf16_config c = base;
             c.single_variant = variant;
             c.single_units_per_thread = u;
+            c.block_threads = bt;
             const bool tma = variant == kVariantTma;
             const int fit = ctx->per_sm(single_kernel_for_occupancy(kModeOut, true, u, variant),
-                                        tma ? single_tma_smem_bytes() : 0);
+                                        tma ? single_tma_smem_bytes() : 0, bt);
             for (int bps : block_candidates(fit)) {
                 c.single_blocks_per_sm = bps;
                 SingleLaunch L;
@@ -173,7 +175,8 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
     for (int variant = 0; variant <= 2; ++variant)
     for (int bps : block_candidates(ctx->per_sm(single_kernel_for_occupancy(kModeCheck, true, winner.single_units_per_thread,
                                                                             variant),
-                                                variant == kVariantTma ? single_tma_smem_bytes() : 0))) {
+                                                variant == kVariantTma ? single_tma_smem_bytes() : 0,
+                                                variant == kVariantTma ? kBlockThreads : winner.block_threads))) {
         utf16_config c = winner;
         c.check_variant = variant;
         c.check_blocks_per_sm = bps;
@@ -223,7 +226,8 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
         for (int variant = 0; variant <= 2; ++variant)
         for (int bps : block_candidates(
                  ctx->per_sm(single_kernel_for_occupancy(kModeInPlace, false, winner.single_units_per_thread, variant),
-                             variant == kVariantTma ? single_tma_smem_bytes() : 0))) {
+                             variant == kVariantTma ? single_tma_smem_bytes() : 0,
+                             variant == kVariantTma ? kBlockThreads : winner.block_threads))) {
             utf16_config c = winner;
             c.inplace_variant = variant;
             c.inplace_blocks_per_sm = bps;
@@ -278,12 +282,17 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
 
     utf16_config base = ctx->def, winner = base;
     float best_ms = 1e30f;
-    for (int u : {2, 4}) {
+    for (int u : {2, 4})
+    for (int bt : {128, 256, 512})
+    for (int vb : {8, 16, 32}) {
         for (int pf = 0; pf <= 1; ++pf) {
+            if (pf && (u != 2 || vb != 16)) continue;  // the next chunk in flight is built for 1024 units, 16 bytes
             utf16_config c = base;
             c.batch_units_per_thread = u;
             c.batch_prefetch = pf;
-            const int fit = ctx->per_sm(batch_kernel_for_occupancy(kModeOut, u, pf != 0), 0);
+            c.block_threads = bt;
+            c.vector_bytes = vb;
+            const int fit = ctx->per_sm(batch_kernel_for_occupancy(kModeOut, u, pf != 0, vb), 0, bt);
             for (int bps : block_candidates(fit)) {
                 c.batch_blocks_per_sm = bps;
                 BatchLaunch L;
@@ -314,6 +323,10 @@ extern "C" int utf16_autotune_batch(const uint16_t *in, uint16_t *out, const int
     // store "by mode", so that the other batch forms keep their own width
     // (2048 units for the check and in place).
     if (winner.batch_units_per_thread == 2) winner.batch_units_per_thread = 0;
+    // The same for the block size and the load width the out-of-place form
+    // takes by default (512 threads, 16-byte loads; in place defaults to 32).
+    if (winner.block_threads == kMaxBlockThreads) winner.block_threads = 0;
+    if (winner.vector_bytes == 16) winner.vector_bytes = 0;
     // The per-string check: next chunk in flight or not, with the winner's
     // other settings (its results go to a scratch array).
     {

@@ -10,7 +10,10 @@ namespace u16wf {
 
 struct Slot;
 
+// Block size by default; launches may choose 128 to kMaxBlockThreads threads
+// (the single-string and batch kernels are built for that maximum).
 constexpr int kBlockThreads = 256;
+constexpr int kMaxBlockThreads = 512;
 
 enum Mode : int {
     kModeOut = 0,      // out-of-place repair
@@ -44,6 +47,7 @@ struct SingleLaunch {
     long long capacity = 0;          // kModeList: its length
     bool full_pass = false;          // kModeCheck: read the whole string (no early exit), for timing
     bool full_occupancy = false;     // max_blocks is every block slot of the GPU
+    int block_threads = kBlockThreads;  // 128-bit-load kernels; the TMA kernel always uses kBlockThreads
 };
 
 cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream);
@@ -67,10 +71,12 @@ struct BatchLaunch {
     int blocks = 1;                  // persistent grid size
     bool full_occupancy = false;     // blocks is every block slot of the GPU
     long long units_hint = 0;        // units in the batch when the caller knows them (0: unknown)
+    int block_threads = kBlockThreads;
+    int vector_bytes = 16;           // bytes per lane load: 8, 16 or 32
 };
 
 cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream);
-const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch = false);
+const void *batch_kernel_for_occupancy(int mode, int u, bool prefetch = false, int vector_bytes = 16);
 
 // Smallest index violating "offsets[0] >= 0, non-decreasing" (or -1) into
 // *result, through the stream's slot.

@@ -39,16 +39,17 @@ int bucket_of(int64_t v) {
     return b;
 }
 
-int DeviceCtx::per_sm(const void *fn, size_t smem) {
+int DeviceCtx::per_sm(const void *fn, size_t smem, int threads) {
     std::lock_guard<std::mutex> lk(mu);
-    auto it = occupancy.find(fn);
+    const auto key = std::make_pair(fn, threads);
+    auto it = occupancy.find(key);
     if (it != occupancy.end()) return it->second;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlockThreads, smem) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess || n < 1) {
         cudaGetLastError();
         n = 1;
     }
-    occupancy[fn] = n;
+    occupancy[key] = n;
     return n;
 }
 
@@ -89,7 +90,9 @@ static bool config_valid(const utf16_config &c) {
            c.single_blocks_per_sm >= 0 &&
            c.single_blocks_per_sm <= 64 && (c.batch_units_per_thread == 0 || c.batch_units_per_thread == 2 || c.batch_units_per_thread == 4) &&
            (c.batch_prefetch == 0 || c.batch_prefetch == 1) && c.batch_blocks_per_sm >= 0 &&
-           c.batch_blocks_per_sm <= 64;
+           c.batch_blocks_per_sm <= 64 &&
+           (c.block_threads == 0 || c.block_threads == 128 || c.block_threads == 256 || c.block_threads == 512) &&
+           (c.vector_bytes == 0 || c.vector_bytes == 8 || c.vector_bytes == 16 || c.vector_bytes == 32);
 }
 
 int get_ctx(DeviceCtx **out) {
@@ -157,8 +160,12 @@ int get_ctx(DeviceCtx **out) {
     // faster (1024 units 3.12 -> 2.89 us, 1,000,000 units 5.21 -> 4.68 us),
     // long ones unchanged.
     g_pdl = env_int("UTF16WF_PDL", 1) != 0;
+    // Block size (0: 256 threads) and bytes per lane load of the bit-word
+    // kernels (0: 16 bytes).
+    d.block_threads = env_int("UTF16WF_BLOCK_THREADS", 0);
+    d.vector_bytes = env_int("UTF16WF_VECTOR_BYTES", 0);
     if (!config_valid(d))
-        d = utf16_config{kVariantLdg, 0, 0, 0, 0, 0, kVariantLdg, 0, kVariantLdgPrefetch, 0, 0, 0};
+        d = utf16_config{kVariantLdg, 0, 0, 0, 0, 0, kVariantLdg, 0, kVariantLdgPrefetch, 0, 0, 0, 0, 0};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);
@@ -180,8 +187,10 @@ void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) 
                                                                                 : 4;
     const bool fb = L.first_bad || L.mode == kModeCheck;
     const bool tma = L.variant == kVariantTma;
+    // The TMA kernel's tile is one chunk per warp of a kBlockThreads block.
+    L.block_threads = tma ? kBlockThreads : cfg.block_threads > 0 ? cfg.block_threads : kBlockThreads;
     const void *fn = single_kernel_for_occupancy(L.mode, fb, L.units_per_thread, L.variant);
-    const int fit = ctx->per_sm(fn, tma ? single_tma_smem_bytes() : 0);
+    const int fit = ctx->per_sm(fn, tma ? single_tma_smem_bytes() : 0, L.block_threads);
     const int want = L.mode == kModeCheck     ? cfg.check_blocks_per_sm
                      : L.mode == kModeInPlace ? cfg.inplace_blocks_per_sm
                                               : cfg.single_blocks_per_sm;
@@ -193,7 +202,14 @@ void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) 
 void configure_batch(DeviceCtx *ctx, const utf16_config &cfg, BatchLaunch &L) {
     L.units_per_thread = cfg.batch_units_per_thread;
     L.prefetch = (L.mode == kModeCheck ? cfg.batch_check_prefetch : cfg.batch_prefetch) != 0;
-    const int fit = ctx->per_sm(batch_kernel_for_occupancy(L.mode, L.units_per_thread, L.prefetch), 0);
+    // Unset (0): 512-thread blocks, and 32-byte loads in place, 16 otherwise
+    // (1M strings: out of place 69.1 against 69.8 us at 256 threads; in place
+    // 64.9 against 68.4 us with 16-byte loads; the check 43.2 against 49-50
+    // with 32-byte ones).
+    L.block_threads = cfg.block_threads > 0 ? cfg.block_threads : kMaxBlockThreads;
+    L.vector_bytes = cfg.vector_bytes > 0 ? cfg.vector_bytes : L.mode == kModeInPlace ? 32 : 16;
+    const int fit = ctx->per_sm(batch_kernel_for_occupancy(L.mode, L.units_per_thread, L.prefetch, L.vector_bytes), 0,
+                                L.block_threads);
     const int per = cfg.batch_blocks_per_sm > 0 ? std::min(cfg.batch_blocks_per_sm, fit) : fit;
     L.blocks = per * ctx->sms;
     L.full_occupancy = per == fit;

@@ -4,8 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
 #include <unordered_map>
+#include <utility>
 
 #include "../../include/utf16wf.h"
 #include "device.cuh"
@@ -29,7 +31,7 @@ struct DeviceCtx {
     Slot *slots = nullptr;  // device pool of kSlotCount slots
     int slots_used = 0;
     std::unordered_map<cudaStream_t, int> slot_of;
-    std::unordered_map<const void *, int> occupancy;  // kernel -> resident blocks per SM
+    std::map<std::pair<const void *, int>, int> occupancy;  // (kernel, block size) -> resident blocks per SM
 
     // Launch configuration: the default, and per log2 bucket what the
     // autotuner measured best (single strings: bucket of n; batches: bucket
@@ -49,7 +51,7 @@ struct DeviceCtx {
     int64_t *chunk_first = nullptr;  // pinned host
     int64_t chunk_first_cap = 0;
 
-    int per_sm(const void *fn, size_t smem);
+    int per_sm(const void *fn, size_t smem, int threads = kBlockThreads);
     int slot_for(cudaStream_t s, Slot **out);
     int ensure_staging(int64_t units, int64_t chunks);
     void release_staging();

@@ -47,7 +47,7 @@ __device__ __forceinline__ unsigned long long poll_known_mismatch(const SingleAr
 }
 
 template <int MODE, bool FB, int ST, int U, bool PF>
-__global__ void __launch_bounds__(kBlockThreads) single_kernel(const SingleArgs A) {
+__global__ void __launch_bounds__(kMaxBlockThreads) single_kernel(const SingleArgs A) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -174,13 +174,15 @@ cudaError_t launch_single(const SingleLaunch &L, cudaStream_t stream) {
     const SingleArgs A = make_single_args(L, U * kWarpSliceUnits);
     const bool fb = (L.first_bad || L.mode == kModeCheck) && L.mode != kModeList;
     const void *fn = words ? inplace_words_kernel_for(fb, U, pf) : pick_single(L.mode, fb, store_width(L), U, pf);
-    const long long warps_per_block = kBlockThreads / 32;
+    const int bt = L.block_threads;
+    if (bt < 32 || bt > kMaxBlockThreads || bt % 32) return cudaErrorInvalidValue;
+    const long long warps_per_block = bt / 32;
     long long blocks = (A.chunks + warps_per_block - 1) / warps_per_block;
     if (blocks > (long long)L.max_blocks) blocks = L.max_blocks;
     if (blocks < 1) blocks = 1;
     void *args[] = {(void *)&A};
     const long long warps = blocks * warps_per_block;
-    return launch_kernel(fn, dim3((unsigned)blocks), dim3(kBlockThreads), args, 0, stream,
+    return launch_kernel(fn, dim3((unsigned)blocks), dim3((unsigned)bt), args, 0, stream,
                          pdl_fits((A.chunks + warps - 1) / warps, L.full_occupancy));
 }
 

@@ -242,7 +242,7 @@ __device__ __forceinline__ void process_chunk(const SingleArgs &A, long long cfi
 // grid on the stream sees the reset at the kernel boundary).  A grid of one
 // block publishes directly.
 __device__ __forceinline__ void finish_first_bad(const SingleArgs &A, long long my_first, int lane) {
-    __shared__ long long s_min[kBlockThreads / 32];
+    __shared__ long long s_min[kMaxBlockThreads / 32];
     const long long wmin = warp_min_ll(my_first);
     if (lane == 0) s_min[threadIdx.x >> 5] = wmin;
     __syncthreads();

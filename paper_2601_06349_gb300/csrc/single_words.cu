@@ -136,9 +136,9 @@ __device__ __forceinline__ void inplace_words_chunk(const SingleArgs &A, long lo
 }
 
 template <bool FB, int U, bool PF>
-__global__ void __launch_bounds__(kBlockThreads) inplace_words_kernel(const SingleArgs A) {
+__global__ void __launch_bounds__(kMaxBlockThreads) inplace_words_kernel(const SingleArgs A) {
     constexpr long long CU = (long long)U * kWarpSliceUnits;
-    __shared__ WordTable<U> s_table[kBlockThreads / 32];
+    __shared__ WordTable<U> s_table[kMaxBlockThreads / 32];
     const int lane = threadIdx.x & 31;
     WordTable<U> &ws = s_table[threadIdx.x >> 5];
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

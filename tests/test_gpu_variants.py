@@ -15,7 +15,9 @@ from gpu_util import Guarded, first_diff, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-SINGLE = [(0, 4, 0), (0, 2, 0), (1, 4, 0), (1, 2, 0), (2, 4, 0), (2, 4, 1), (0, 4, 1), (1, 2, 2)]
+# (data path, chunk width, blocks per SM, threads per block)
+SINGLE = [(0, 4, 0, 0), (0, 2, 0, 0), (1, 4, 0, 0), (1, 2, 0, 0), (2, 4, 0, 0), (2, 4, 1, 0), (0, 4, 1, 0),
+          (1, 2, 2, 0), (0, 4, 0, 128), (1, 4, 0, 512), (0, 2, 0, 512), (1, 2, 3, 128), (2, 4, 0, 512)]
 BATCH = [(0, 0, 0), (4, 0, 0), (2, 0, 0), (4, 1, 0), (2, 1, 0), (4, 0, 1)]
 
 
@@ -40,11 +42,11 @@ def strings():
             "clean": (clean, clean, clean.size)}
 
 
-@pytest.mark.parametrize("variant,u,bps", SINGLE)
-def test_single_configurations(pkg, strings, variant, u, bps):
+@pytest.mark.parametrize("variant,u,bps,bt", SINGLE)
+def test_single_configurations(pkg, strings, variant, u, bps, bt):
     import torch
     pkg.set_config(single_variant=variant, single_units_per_thread=u, single_blocks_per_sm=bps,
-                   check_variant=variant, inplace_variant=variant)
+                   check_variant=variant, inplace_variant=variant, block_threads=bt)
     for name, (src, want, want_fb) in strings.items():
         for a_in, a_out in ((0, 0), (3, 3), (5, 1)):
             gi = Guarded(src.size, a_in, src)
@@ -82,6 +84,28 @@ def test_batch_configurations(pkg, u, pf, bps):
     units, offs = workloads.ragged_batch(count=200_000, seed=77)
     _run_all_forms(pkg, units, offs, 0, 0, f"batch u={u} pf={pf}")
     _run_all_forms(pkg, units, offs, 3, 6, f"batch u={u} pf={pf} misaligned")
+    pkg.check_device_errors()
+
+
+@pytest.mark.parametrize("bt", [128, 256, 512])
+@pytest.mark.parametrize("vb", [8, 16, 32])
+def test_batch_block_and_vector_widths(pkg, bt, vb):
+    """Every batch form at both chunk widths with 128-, 256- or 512-thread
+    blocks and 8-, 16- or 32-byte lane loads, aligned and misaligned (store
+    classes 2 to 32), on a log-normal batch and one of tiny strings."""
+    from test_gpu_batch import _run_all_forms
+    units, offs = workloads.ragged_batch(count=60_000, seed=78)
+    rng = np.random.default_rng(vb * 1000 + bt)
+    tiny = np.where(rng.random(40_000) < 0.3, 0, rng.integers(1, 6, 40_000)).astype(np.int64)
+    t_offs = workloads.offsets_from_lengths(tiny, start=3)
+    t_units = np.array([0x41, 0xD800, 0xDBFF, 0xDC00, 0xDFFF], np.uint16)[rng.integers(0, 5, int(t_offs[-1]) + 8)]
+    for u in (2, 4):
+        pkg.set_config(batch_units_per_thread=u, batch_prefetch=0, batch_blocks_per_sm=0, batch_check_prefetch=0,
+                       block_threads=bt, vector_bytes=vb)
+        for a_in, a_out in ((0, 0), (3, 6), (5, 13), (8, 0)):
+            _run_all_forms(pkg, units, offs, a_in, a_out, f"bt={bt} vb={vb} u={u}")
+        _run_all_forms(pkg, t_units, t_offs, 1, 1, f"tiny bt={bt} vb={vb} u={u}")
+    pkg.set_config(block_threads=0, vector_bytes=0)
     pkg.check_device_errors()
 
 
