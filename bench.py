@@ -606,14 +606,24 @@ def ragged_measure(torch, wf, stream):
         wf.to_well_formed_batch(d_u, d_o, d_out, stream=stream)
     g_rep = capture_graph(torch, lambda: wf.to_well_formed_batch(d_u, d_o, d_out))
     g_chk = capture_graph(torch, lambda: wf.first_error_index_batch(d_u, d_o, fbb))
-    ms = time_launches(torch, g_rep.replay, steps, stream) / steps
-    ms_chk = time_launches(torch, g_chk.replay, steps, stream) / steps
+    # five trials of `steps` replays each: the median, and the range beside it
+    trials = 5
+    t_rep = sorted(time_launches(torch, g_rep.replay, steps, stream) / steps for _ in range(trials))
+    t_chk = sorted(time_launches(torch, g_chk.replay, steps, stream) / steps for _ in range(trials))
+    ms, ms_chk = t_rep[trials // 2], t_chk[trials // 2]
     peak, _ = measured_peaks()
     algo = total * 4 + offs.size * 8
+    algo_chk = total * 2 + offs.size * 16
     res = {"strings": int(offs.size - 1), "units": total, "launch": "CUDA graph replay of the persistent kernel",
+           "timing": f"median of {trials} trials of {steps} back-to-back replays",
            "batch_input_gbs": round(total * 2 / (ms * 1e-3) / 1e9, 1),
            "batch_hbm_frac": round(algo / (ms * 1e-3) / 1e9 / peak, 4), "batch_ms": round(ms, 4),
-           "check_input_gbs": round(total * 2 / (ms_chk * 1e-3) / 1e9, 1), "check_ms": round(ms_chk, 4)}
+           "batch_us_range": [round(t_rep[0] * 1e3, 2), round(t_rep[-1] * 1e3, 2)],
+           "check_input_gbs": round(total * 2 / (ms_chk * 1e-3) / 1e9, 1), "check_ms": round(ms_chk, 4),
+           "check_hbm_frac": round(algo_chk / (ms_chk * 1e-3) / 1e9 / peak, 4),
+           "check_us_range": [round(t_chk[0] * 1e3, 2), round(t_chk[-1] * 1e3, 2)],
+           "bytes": "repair: 4 B per unit + 8 B per string (offsets); check: 2 B per unit + 16 B per string "
+                    "(offsets read, first_bad written)"}
     # per-string plain launches on a sample of consecutive strings
     sample = 20000
     lens = np.diff(offs[: sample + 1])
