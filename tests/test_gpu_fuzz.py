@@ -110,3 +110,51 @@ def test_fuzz_ragged_batches(pkg, seed):
         pkg.to_well_formed_batch_(gi.view, d_off)
         assert np.array_equal(gi.get(), want), (seed, it)
         assert gi.canaries_ok()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fuzz_ragged_launch_shapes(pkg, seed):
+    """Random ragged batches under a random launch shape each: chunk width,
+    block size, lane load width, next chunk in flight and blocks per SM, with
+    the input and a separate output misaligned at random (every store class).
+    Units of the output outside [offsets[0], offsets[count]) keep their
+    canary value, as the entry points promise."""
+    import torch
+    from gpu_util import CANARY
+    rng = np.random.default_rng(3000 + seed)
+    try:
+        for it in range(16):
+            cfg = dict(batch_units_per_thread=int(rng.choice([2, 4])), block_threads=int(rng.choice([128, 256, 512])),
+                       vector_bytes=int(rng.choice([8, 16, 32])), batch_prefetch=int(rng.integers(0, 2)),
+                       batch_check_prefetch=int(rng.integers(0, 2)), batch_blocks_per_sm=int(rng.integers(0, 3)))
+            pkg.set_config(**cfg)
+            count = int(rng.integers(1, 4000))
+            r = rng.random(count)
+            lens = np.where(r < 0.25, 0, np.where(r < 0.85, rng.integers(1, 120, count),
+                                                  rng.integers(120, 9000, count)))
+            start = int(rng.integers(0, 40))
+            offs = workloads.offsets_from_lengths(lens.astype(np.int64), start=start)
+            total = int(offs[-1]) + int(rng.integers(0, 40))
+            units = _random_string(rng, total)
+            want = oracle.to_well_formed_batch(units, offs)
+            want_fb = oracle.first_bad_batch(units, offs)
+            lo, hi = int(offs[0]), int(offs[-1])
+            a_in, a_out = int(rng.integers(0, 16)), int(rng.integers(0, 16))
+            gi = Guarded(max(total, 1), a_in, units if total else np.zeros(1, np.uint16))
+            go = Guarded(max(total, 1), a_out)
+            vi, vo = gi.view[:total], go.view[:total]
+            d_off = torch.from_numpy(offs).cuda()
+            pkg.to_well_formed_batch(vi, d_off, vo)
+            got = to_host(vo)
+            tag = (seed, it, cfg, a_in, a_out, count, total)
+            assert np.array_equal(got[lo:hi], want[lo:hi]), (tag, first_diff(got[lo:hi], want[lo:hi]))
+            assert np.all(got[:lo] == CANARY) and np.all(got[hi:] == CANARY), tag
+            fb = pkg.first_error_index_batch(vi, d_off).cpu().numpy()
+            assert np.array_equal(fb, want_fb), (tag, first_diff(fb, want_fb))
+            pkg.to_well_formed_batch_(vi, d_off)
+            assert np.array_equal(to_host(vi), want), tag
+            assert gi.canaries_ok() and go.canaries_ok(), tag
+    finally:
+        pkg.set_config(batch_units_per_thread=0, block_threads=0, vector_bytes=0, batch_prefetch=0,
+                       batch_check_prefetch=0, batch_blocks_per_sm=0)
+    pkg.check_device_errors()
