@@ -122,8 +122,9 @@ def test_fuzz_ragged_launch_shapes(pkg, seed):
     import torch
     from gpu_util import CANARY
     rng = np.random.default_rng(3000 + seed)
+    saved = pkg.get_config()
     try:
-        for it in range(16):
+        for it in range(40):
             cfg = dict(batch_units_per_thread=int(rng.choice([2, 4])), block_threads=int(rng.choice([128, 256, 512])),
                        vector_bytes=int(rng.choice([8, 16, 32])), batch_prefetch=int(rng.integers(0, 2)),
                        batch_check_prefetch=int(rng.integers(0, 2)), batch_blocks_per_sm=int(rng.integers(0, 3)))
@@ -155,6 +156,42 @@ def test_fuzz_ragged_launch_shapes(pkg, seed):
             assert np.array_equal(to_host(vi), want), tag
             assert gi.canaries_ok() and go.canaries_ok(), tag
     finally:
-        pkg.set_config(batch_units_per_thread=0, block_threads=0, vector_bytes=0, batch_prefetch=0,
-                       batch_check_prefetch=0, batch_blocks_per_sm=0)
+        pkg.set_config(saved)
+    pkg.check_device_errors()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fuzz_single_launch_shapes(pkg, seed):
+    """Random single strings under a random launch shape each: data path of
+    the repair, the check and in-place repair (128-bit loads, next chunk in
+    flight, TMA), units per thread, unit stores in place, block size and
+    blocks per SM, at random input and output misalignment."""
+    rng = np.random.default_rng(4000 + seed)
+    saved = pkg.get_config()
+    try:
+        for it in range(80):
+            cfg = dict(single_variant=int(rng.integers(0, 3)), check_variant=int(rng.integers(0, 3)),
+                       inplace_variant=int(rng.integers(0, 3)), single_units_per_thread=int(rng.choice([0, 2, 4])),
+                       inplace_unit_stores=int(rng.integers(0, 2)), block_threads=int(rng.choice([0, 128, 256, 512])),
+                       single_blocks_per_sm=int(rng.integers(0, 4)), check_blocks_per_sm=int(rng.integers(0, 4)),
+                       inplace_blocks_per_sm=int(rng.integers(0, 4)))
+            pkg.set_config(**cfg)
+            n = _length(rng)
+            u = _random_string(rng, n)
+            want = oracle.to_well_formed(u)
+            want_fb = oracle.first_bad(u)
+            a_in, a_out = int(rng.integers(0, 8)), int(rng.integers(0, 8))
+            gi = Guarded(max(n, 1), a_in, u if n else np.zeros(1, np.uint16))
+            go = Guarded(max(n, 1), a_out)
+            vi, vo = gi.view[:n], go.view[:n]
+            tag = (seed, it, cfg, n, a_in, a_out)
+            _, fb = pkg.to_well_formed_first_bad(vi, vo)
+            assert np.array_equal(to_host(vo), want), (tag, first_diff(to_host(vo), want))
+            assert int(fb.item()) == want_fb, tag
+            assert int(pkg.first_error_index(vi).item()) == want_fb, tag
+            pkg.to_well_formed_(vi)
+            assert np.array_equal(to_host(vi), want), tag
+            assert gi.canaries_ok() and go.canaries_ok(), tag
+    finally:
+        pkg.set_config(saved)
     pkg.check_device_errors()
