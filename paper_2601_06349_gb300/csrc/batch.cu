@@ -10,13 +10,36 @@ namespace u16wf {
 // first_bad[s] = length of string s (the value for a well-formed string).
 // The next grid (the check) may start as soon as this one has waited for
 // its own predecessors: it reads only what those wrote before its first
-// atomic on first_bad, where it waits for this grid.
+// atomic on first_bad, where it waits for this grid, so this grid's
+// duration is on the check's path.  Each thread takes kLengthsPerThread
+// strings (a block stride apart, so that every load is coalesced) and issues
+// all their loads before its first store: one memory latency per pass
+// instead of one per string (1M strings: the check 43.1 -> 41.8 us; one
+// string per thread in 4x the blocks 44.7).
+constexpr int kLengthsPerThread = 4;
 __global__ void batch_lengths_kernel(const long long *offsets, long long count, long long *first_bad) {
     wait_prior_grids();
     allow_next_grid();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
-        first_bad[i] = offsets[i + 1] - offsets[i];
+    constexpr int K = kLengthsPerThread;
+    const long long stride = (long long)gridDim.x * blockDim.x * K;
+    for (long long b = (long long)blockIdx.x * blockDim.x * K + threadIdx.x; b < count; b += stride) {
+        long long s[K], e[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const long long i = b + (long long)k * blockDim.x;
+            s[k] = 0;
+            e[k] = 0;
+            if (i < count) {
+                s[k] = offsets[i];
+                e[k] = offsets[i + 1];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const long long i = b + (long long)k * blockDim.x;
+            if (i < count) first_bad[i] = e[k] - s[k];
+        }
+    }
 }
 
 // Chunk width of each form when the configuration leaves it open (0):
@@ -50,8 +73,10 @@ cudaError_t launch_batch(const BatchLaunch &L, cudaStream_t stream) {
     const void *fn = pick_batch(L.mode, st, nw, vb, L.prefetch);
     if (!fn) return cudaErrorInvalidValue;
     if (L.mode == kModeCheck || L.mode == kModeInPlaceFirst) {
-        long long blocks = (L.count + kBlockThreads - 1) / kBlockThreads;
-        if (blocks > L.blocks) blocks = L.blocks;
+        // One pass over the strings where it fits in four times the batch
+        // kernel's grid.
+        long long blocks = (L.count + kBlockThreads * kLengthsPerThread - 1) / (kBlockThreads * kLengthsPerThread);
+        if (blocks > 4LL * L.blocks) blocks = 4LL * L.blocks;
         if (blocks < 1) blocks = 1;
         const long long *offsets = L.offsets;
         long long count = L.count;
