@@ -247,6 +247,15 @@ typedef struct {
     int vector_bytes;            /* bytes each lane loads at once in the batch kernels: 8, 16 or 32 (256-bit
                                     loads); 0 (default) = 32 for in-place batch repair, 16 for the other batch
                                     forms.  Single strings use 16 */
+    int repair_variant;          /* out-of-place repair without the first-error index (utf16_to_well_formed,
+                                    single strings): 0, 1 or 2 as single_variant; -1 (default) = single_variant.
+                                    Its kernel keeps no first-error state, so its best data path can differ */
+    int repair_units_per_thread; /* the same repair: 2 or 4; 0 (default) = single_units_per_thread */
+    int repair_blocks_per_sm;    /* the same repair: persistent grid = SMs x this, 0 = as many as fit;
+                                    -1 (default) = single_blocks_per_sm */
+    int repair_block_threads;    /* threads per block of single strings, by form: the repair without the */
+    int check_block_threads;     /* first-error index, the read-only check, in-place repair; 128, 256 or */
+    int inplace_block_threads;   /* 512; 0 (default) = block_threads.  The TMA data path always uses 256 */
 } utf16_config;
 
 /* Default configuration of the current device (used where nothing is tuned). */
@@ -262,7 +271,8 @@ int utf16_set_config(const utf16_config *cfg);
  * each, the fastest trial counting; synchronous.
  * The fastest is stored for the size bucket floor(log2(n)) of single strings
  * (utf16_autotune_single: out-of-place repair with first-error index; then
- * the data path and grid of the read-only check, timed on the repaired
+ * the data path, chunk width and grid of the out-of-place repair without it;
+ * then the data path and grid of the read-only check, timed on the repaired
  * (well-formed) string in `out`, and of in-place repair, timed on copies of
  * `in`) or for
  * the bucket floor(log2(num_strings)) of batches (utf16_autotune_batch, the

@@ -39,7 +39,15 @@ class Config(ctypes.Structure):
                 ("check_variant", ctypes.c_int), ("inplace_unit_stores", ctypes.c_int),
                 ("inplace_variant", ctypes.c_int), ("check_blocks_per_sm", ctypes.c_int),
                 ("inplace_blocks_per_sm", ctypes.c_int), ("batch_check_prefetch", ctypes.c_int),
-                ("block_threads", ctypes.c_int), ("vector_bytes", ctypes.c_int)]
+                ("block_threads", ctypes.c_int), ("vector_bytes", ctypes.c_int),
+                ("repair_variant", ctypes.c_int), ("repair_units_per_thread", ctypes.c_int),
+                ("repair_blocks_per_sm", ctypes.c_int), ("repair_block_threads", ctypes.c_int),
+                ("check_block_threads", ctypes.c_int), ("inplace_block_threads", ctypes.c_int)]
+    # Fields whose "not set" value is -1 (0 is a setting of its own).
+    _UNSET = {"repair_variant": -1, "repair_blocks_per_sm": -1}
+
+    def __init__(self, **fields):
+        super().__init__(**{**self._UNSET, **fields})
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -71,11 +71,13 @@ bool tune_log() {
 void log_candidate(const char *what, const utf16_config &c, float ms) {
     if (!tune_log()) return;
     fprintf(stderr,
-            "utf16wf tune %s: single v%d U%d bps%d | check v%d bps%d | inplace v%d bps%d | batch U%d pf%d bps%d "
-            "check-pf%d | threads %d vector %d: %.4f ms\n",
-            what, c.single_variant, c.single_units_per_thread, c.single_blocks_per_sm, c.check_variant,
-            c.check_blocks_per_sm, c.inplace_variant, c.inplace_blocks_per_sm, c.batch_units_per_thread,
-            c.batch_prefetch, c.batch_blocks_per_sm, c.batch_check_prefetch, c.block_threads, c.vector_bytes, ms);
+            "utf16wf tune %s: single v%d U%d bps%d | repair v%d U%d bps%d t%d | check v%d bps%d t%d | inplace v%d "
+            "bps%d t%d | batch U%d pf%d bps%d check-pf%d | threads %d vector %d: %.4f ms\n",
+            what, c.single_variant, c.single_units_per_thread, c.single_blocks_per_sm, c.repair_variant,
+            c.repair_units_per_thread, c.repair_blocks_per_sm, c.repair_block_threads, c.check_variant,
+            c.check_blocks_per_sm, c.check_block_threads, c.inplace_variant, c.inplace_blocks_per_sm,
+            c.inplace_block_threads, c.batch_units_per_thread, c.batch_prefetch, c.batch_blocks_per_sm,
+            c.batch_check_prefetch, c.block_threads, c.vector_bytes, ms);
 }
 
 // Fastest of three trials of `reps` back-to-back launches (ms per trial):
@@ -166,6 +168,64 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
             }
         }
     }
+    // The repair without the first-error index on its own: its kernel keeps
+    // no first-error state, so a data path that costs the fused kernel
+    // occupancy can be its fastest (1 GiB at 1e-2: next chunk in flight,
+    // 332 against 343 us).  Kept only where it beats following the fused
+    // form's settings (-1 / 0 / -1).
+    {
+        auto time_plain = [&](const utf16_config &c, float *ms) -> bool {
+            SingleLaunch L;
+            L.in = in;
+            L.out = out;
+            L.n = n;
+            L.mode = kModeOut;
+            L.first_bad = false;
+            configure_single(ctx, c, L);
+            if (launch_single(L, t.s) != cudaSuccess) return false;
+            return time_trials(t, reps, [&] { return launch_single(L, t.s) == cudaSuccess; }, ms, &scrub);
+        };
+        utf16_config plain_winner = winner;
+        plain_winner.repair_variant = -1;
+        plain_winner.repair_units_per_thread = 0;
+        plain_winner.repair_blocks_per_sm = -1;
+        plain_winner.repair_block_threads = 0;
+        float best_plain = 0.f;
+        if (!time_plain(plain_winner, &best_plain)) {
+            cudaGetLastError();
+            return UTF16_ECUDA;
+        }
+        log_candidate("repair (as the fused form)", plain_winner, best_plain);
+        for (int variant = 0; variant <= 2; ++variant)
+            for (int u : {2, 4})
+            for (int bt : {128, 256, 512}) {
+                const bool tma = variant == kVariantTma;
+                if (tma && (u != 4 || bt != kBlockThreads)) continue;
+                const int fit = ctx->per_sm(single_kernel_for_occupancy(kModeOut, false, u, variant),
+                                            tma ? single_tma_smem_bytes() : 0, bt);
+                for (int bps : block_candidates(fit)) {
+                    utf16_config c = winner;
+                    c.repair_variant = variant;
+                    c.repair_units_per_thread = u;
+                    c.repair_blocks_per_sm = bps;
+                    c.repair_block_threads = bt;
+                    float ms = 0.f;
+                    if (!time_plain(c, &ms)) {
+                        cudaGetLastError();
+                        return UTF16_ECUDA;
+                    }
+                    log_candidate("repair", c, ms);
+                    if (ms < best_plain) {
+                        best_plain = ms;
+                        plain_winner = c;
+                    }
+                }
+            }
+        winner.repair_variant = plain_winner.repair_variant;
+        winner.repair_units_per_thread = plain_winner.repair_units_per_thread;
+        winner.repair_blocks_per_sm = plain_winner.repair_blocks_per_sm;
+        winner.repair_block_threads = plain_winner.repair_block_threads;
+    }
     // The read-only check separately: each data path and grid on `out`, which
     // now holds the repaired (well-formed) string, so that every candidate
     // reads the whole string as for valid input (full_pass also turns off the
@@ -173,13 +233,16 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
     float best_check = 1e30f;
     utf16_config check_winner = winner;
     for (int variant = 0; variant <= 2; ++variant)
+    for (int bt : {128, 256, 512})
     for (int bps : block_candidates(ctx->per_sm(single_kernel_for_occupancy(kModeCheck, true, winner.single_units_per_thread,
                                                                             variant),
                                                 variant == kVariantTma ? single_tma_smem_bytes() : 0,
-                                                variant == kVariantTma ? kBlockThreads : winner.block_threads))) {
+                                                variant == kVariantTma ? kBlockThreads : bt))) {
+        if (variant == kVariantTma && bt != kBlockThreads) continue;
         utf16_config c = winner;
         c.check_variant = variant;
         c.check_blocks_per_sm = bps;
+        c.check_block_threads = bt;
         SingleLaunch L;
         L.in = out;
         L.n = n;
@@ -206,6 +269,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
     }
     winner.check_variant = check_winner.check_variant;
     winner.check_blocks_per_sm = check_winner.check_blocks_per_sm;
+    winner.check_block_threads = check_winner.check_block_threads;
     // In-place repair: each data path on a fresh copy of `in` in `out` per
     // launch; the copies alone are timed too and subtracted.
     {
@@ -224,13 +288,16 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
         float best_inplace = 1e30f;
         utf16_config inplace_winner = winner;
         for (int variant = 0; variant <= 2; ++variant)
+        for (int bt : {128, 256, 512})
         for (int bps : block_candidates(
                  ctx->per_sm(single_kernel_for_occupancy(kModeInPlace, false, winner.single_units_per_thread, variant),
                              variant == kVariantTma ? single_tma_smem_bytes() : 0,
-                             variant == kVariantTma ? kBlockThreads : winner.block_threads))) {
+                             variant == kVariantTma ? kBlockThreads : bt))) {
+            if (variant == kVariantTma && bt != kBlockThreads) continue;
             utf16_config c = winner;
             c.inplace_variant = variant;
             c.inplace_blocks_per_sm = bps;
+            c.inplace_block_threads = bt;
             SingleLaunch L;
             L.in = out;
             L.out = out;
@@ -250,6 +317,7 @@ extern "C" int utf16_autotune_single(const uint16_t *in, uint16_t *out, int64_t 
         }
         winner.inplace_variant = inplace_winner.inplace_variant;
         winner.inplace_blocks_per_sm = inplace_winner.inplace_blocks_per_sm;
+        winner.inplace_block_threads = inplace_winner.inplace_block_threads;
     }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);

@@ -80,6 +80,8 @@ utf16_config DeviceCtx::batch_config(int64_t units, int64_t count) {
     return batch_has[b] ? batch_tuned[b] : def;
 }
 
+static bool threads_valid(int t) { return t == 0 || t == 128 || t == 256 || t == 512; }
+
 static bool config_valid(const utf16_config &c) {
     return c.single_variant >= 0 && c.single_variant <= 2 && c.check_variant >= 0 && c.check_variant <= 2 &&
            c.inplace_variant >= 0 && c.inplace_variant <= 2 && c.check_blocks_per_sm >= 0 &&
@@ -92,7 +94,11 @@ static bool config_valid(const utf16_config &c) {
            (c.batch_prefetch == 0 || c.batch_prefetch == 1) && c.batch_blocks_per_sm >= 0 &&
            c.batch_blocks_per_sm <= 64 &&
            (c.block_threads == 0 || c.block_threads == 128 || c.block_threads == 256 || c.block_threads == 512) &&
-           (c.vector_bytes == 0 || c.vector_bytes == 8 || c.vector_bytes == 16 || c.vector_bytes == 32);
+           (c.vector_bytes == 0 || c.vector_bytes == 8 || c.vector_bytes == 16 || c.vector_bytes == 32) &&
+           c.repair_variant >= -1 && c.repair_variant <= 2 &&
+           (c.repair_units_per_thread == 0 || c.repair_units_per_thread == 2 || c.repair_units_per_thread == 4) &&
+           c.repair_blocks_per_sm >= -1 && c.repair_blocks_per_sm <= 64 && threads_valid(c.repair_block_threads) &&
+           threads_valid(c.check_block_threads) && threads_valid(c.inplace_block_threads);
 }
 
 int get_ctx(DeviceCtx **out) {
@@ -164,8 +170,16 @@ int get_ctx(DeviceCtx **out) {
     // kernels (0: 16 bytes).
     d.block_threads = env_int("UTF16WF_BLOCK_THREADS", 0);
     d.vector_bytes = env_int("UTF16WF_VECTOR_BYTES", 0);
+    // The repair without the first-error index follows the fused form's
+    // data path, chunk width and grid unless set (or tuned) on its own.
+    d.repair_variant = env_int("UTF16WF_REPAIR_VARIANT", -1);
+    d.repair_units_per_thread = env_int("UTF16WF_REPAIR_U", 0);
+    d.repair_blocks_per_sm = env_int("UTF16WF_REPAIR_BLOCKS_PER_SM", -1);
+    d.repair_block_threads = env_int("UTF16WF_REPAIR_BLOCK_THREADS", 0);
+    d.check_block_threads = env_int("UTF16WF_CHECK_BLOCK_THREADS", 0);
+    d.inplace_block_threads = env_int("UTF16WF_INPLACE_BLOCK_THREADS", 0);
     if (!config_valid(d))
-        d = utf16_config{kVariantLdg, 0, 0, 0, 0, 0, kVariantLdg, 0, kVariantLdgPrefetch, 0, 0, 0, 0, 0};
+        d = utf16_config{kVariantLdg, 0, 0, 0, 0, 0, kVariantLdg, 0, kVariantLdgPrefetch, 0, 0, 0, 0, 0, -1, 0, -1, 0, 0, 0};
     c->def = d;
     *out = c.get();
     g_ctx[dev] = std::move(c);
@@ -173,8 +187,14 @@ int get_ctx(DeviceCtx **out) {
 }
 
 void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) {
-    L.variant = L.mode == kModeCheck ? cfg.check_variant : L.mode == kModeInPlace ? cfg.inplace_variant
-                                                                                    : cfg.single_variant;
+    // The out-of-place repair without the first-error index has settings of
+    // its own where they are set (1 GiB at 1e-2: next chunk in flight, 0.953
+    // of the copy peak, against 0.923 with the fused form's plain loads).
+    const bool plain = L.mode == kModeOut && !L.first_bad;
+    L.variant = L.mode == kModeCheck     ? cfg.check_variant
+                : L.mode == kModeInPlace ? cfg.inplace_variant
+                : plain && cfg.repair_variant >= 0 ? cfg.repair_variant
+                                                   : cfg.single_variant;
     L.unit_stores = L.mode == kModeInPlace && cfg.inplace_unit_stores != 0;
     // Unit stores exist in the 128-bit-load kernels only.
     if (L.unit_stores && L.variant == kVariantTma) L.variant = kVariantLdg;
@@ -182,18 +202,24 @@ void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) 
     // the string over more warps and SMs (1M units: 3.2-3.5 against 4.4 us
     // per call back to back; from 8M units on, 4-vector chunks are as fast or
     // faster, and 23 against 31 us in place at 64M).
-    L.units_per_thread = cfg.single_units_per_thread != 0 ? cfg.single_units_per_thread
-                         : L.n < (long long)ctx->sms * kAutoWideChunkUnitsPerSm ? 2
-                                                                                : 4;
+    const int cfg_u = plain && cfg.repair_units_per_thread != 0 ? cfg.repair_units_per_thread
+                                                                 : cfg.single_units_per_thread;
+    L.units_per_thread = cfg_u != 0 ? cfg_u : L.n < (long long)ctx->sms * kAutoWideChunkUnitsPerSm ? 2 : 4;
     const bool fb = L.first_bad || L.mode == kModeCheck;
     const bool tma = L.variant == kVariantTma;
     // The TMA kernel's tile is one chunk per warp of a kBlockThreads block.
-    L.block_threads = tma ? kBlockThreads : cfg.block_threads > 0 ? cfg.block_threads : kBlockThreads;
+    const int form_bt = L.mode == kModeCheck     ? cfg.check_block_threads
+                        : L.mode == kModeInPlace ? cfg.inplace_block_threads
+                        : plain                  ? cfg.repair_block_threads
+                                                 : 0;
+    const int bt = form_bt > 0 ? form_bt : cfg.block_threads;
+    L.block_threads = tma ? kBlockThreads : bt > 0 ? bt : kBlockThreads;
     const void *fn = single_kernel_for_occupancy(L.mode, fb, L.units_per_thread, L.variant);
     const int fit = ctx->per_sm(fn, tma ? single_tma_smem_bytes() : 0, L.block_threads);
-    const int want = L.mode == kModeCheck     ? cfg.check_blocks_per_sm
-                     : L.mode == kModeInPlace ? cfg.inplace_blocks_per_sm
-                                              : cfg.single_blocks_per_sm;
+    const int want = L.mode == kModeCheck                    ? cfg.check_blocks_per_sm
+                     : L.mode == kModeInPlace                ? cfg.inplace_blocks_per_sm
+                     : plain && cfg.repair_blocks_per_sm >= 0 ? cfg.repair_blocks_per_sm
+                                                              : cfg.single_blocks_per_sm;
     const int per = want > 0 ? std::min(want, fit) : fit;
     L.max_blocks = per * ctx->sms;
     L.full_occupancy = per == fit;

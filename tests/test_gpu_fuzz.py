@@ -163,9 +163,9 @@ def test_fuzz_ragged_launch_shapes(pkg, seed):
 @pytest.mark.parametrize("seed", range(3))
 def test_fuzz_single_launch_shapes(pkg, seed):
     """Random single strings under a random launch shape each: data path of
-    the repair, the check and in-place repair (128-bit loads, next chunk in
-    flight, TMA), units per thread, unit stores in place, block size and
-    blocks per SM, at random input and output misalignment."""
+    the fused repair, the plain repair, the check and in-place repair (128-bit
+    loads, next chunk in flight, TMA), units per thread, unit stores in place,
+    block size and blocks per SM, at random input and output misalignment."""
     rng = np.random.default_rng(4000 + seed)
     saved = pkg.get_config()
     try:
@@ -174,7 +174,11 @@ def test_fuzz_single_launch_shapes(pkg, seed):
                        inplace_variant=int(rng.integers(0, 3)), single_units_per_thread=int(rng.choice([0, 2, 4])),
                        inplace_unit_stores=int(rng.integers(0, 2)), block_threads=int(rng.choice([0, 128, 256, 512])),
                        single_blocks_per_sm=int(rng.integers(0, 4)), check_blocks_per_sm=int(rng.integers(0, 4)),
-                       inplace_blocks_per_sm=int(rng.integers(0, 4)))
+                       inplace_blocks_per_sm=int(rng.integers(0, 4)), repair_variant=int(rng.integers(-1, 3)),
+                       repair_units_per_thread=int(rng.choice([0, 2, 4])), repair_blocks_per_sm=int(rng.integers(-1, 3)),
+                       repair_block_threads=int(rng.choice([0, 128, 256, 512])),
+                       check_block_threads=int(rng.choice([0, 128, 256, 512])),
+                       inplace_block_threads=int(rng.choice([0, 128, 256, 512])))
             pkg.set_config(**cfg)
             n = _length(rng)
             u = _random_string(rng, n)
@@ -185,6 +189,8 @@ def test_fuzz_single_launch_shapes(pkg, seed):
             go = Guarded(max(n, 1), a_out)
             vi, vo = gi.view[:n], go.view[:n]
             tag = (seed, it, cfg, n, a_in, a_out)
+            pkg.to_well_formed(vi, vo)
+            assert np.array_equal(to_host(vo), want), (tag, "plain", first_diff(to_host(vo), want))
             _, fb = pkg.to_well_formed_first_bad(vi, vo)
             assert np.array_equal(to_host(vo), want), (tag, first_diff(to_host(vo), want))
             assert int(fb.item()) == want_fb, tag

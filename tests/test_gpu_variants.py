@@ -45,8 +45,22 @@ def strings():
 @pytest.mark.parametrize("variant,u,bps,bt", SINGLE)
 def test_single_configurations(pkg, strings, variant, u, bps, bt):
     import torch
+    # the plain repair (no first-error index) on its own settings: this shape,
+    # with the fused form on another data path
+    pkg.set_config(single_variant=(variant + 1) % 3, single_units_per_thread=u, single_blocks_per_sm=bps,
+                   check_variant=variant, inplace_variant=variant, block_threads=bt, repair_variant=variant,
+                   repair_units_per_thread=u, repair_blocks_per_sm=bps)
+    for name, (src, want, want_fb) in strings.items():
+        for a_in, a_out in ((0, 0), (3, 3), (5, 1)):
+            gi = Guarded(src.size, a_in, src)
+            go = Guarded(src.size, a_out)
+            pkg.to_well_formed(gi.view, go.view)
+            got = go.get()
+            assert np.array_equal(got, want), (name, variant, u, a_in, a_out, "plain", first_diff(got, want))
+            assert go.canaries_ok()
     pkg.set_config(single_variant=variant, single_units_per_thread=u, single_blocks_per_sm=bps,
-                   check_variant=variant, inplace_variant=variant, block_threads=bt)
+                   check_variant=variant, inplace_variant=variant, block_threads=bt, repair_variant=-1,
+                   repair_units_per_thread=0, repair_blocks_per_sm=-1)
     for name, (src, want, want_fb) in strings.items():
         for a_in, a_out in ((0, 0), (3, 3), (5, 1)):
             gi = Guarded(src.size, a_in, src)
@@ -155,6 +169,24 @@ def test_batch_window_straddles_chunk_end(pkg, u, pf, bps):
     pkg.check_device_errors()
 
 
+def test_config_fields_by_form_are_validated(pkg):
+    """The settings of the plain repair and the per-form block sizes accept
+    their documented values and reject others (nothing is changed then)."""
+    saved = pkg.get_config()
+    try:
+        pkg.set_config(repair_variant=2, repair_units_per_thread=4, repair_blocks_per_sm=0, repair_block_threads=512,
+                       check_block_threads=128, inplace_block_threads=256)
+        for field, bad in (("repair_variant", 3), ("repair_variant", -2), ("repair_units_per_thread", 3),
+                           ("repair_blocks_per_sm", -2), ("repair_block_threads", 64), ("check_block_threads", 1024),
+                           ("inplace_block_threads", 300)):
+            before = pkg.get_config().as_dict()
+            with pytest.raises(pkg.Utf16Error):
+                pkg.set_config(**{field: bad})
+            assert pkg.get_config().as_dict() == before, field
+    finally:
+        pkg.set_config(saved)
+
+
 def test_autotuner_choice_is_correct(pkg):
     import torch
     u = workloads.mixed(64 << 20, 1e-2, seed=51)
@@ -162,10 +194,20 @@ def test_autotuner_choice_is_correct(pkg):
     out = torch.empty_like(d)
     cfg = pkg.autotune_single(d, out, reps=3)
     assert cfg.single_variant in (0, 1, 2)
+    assert cfg.repair_variant in (-1, 0, 1, 2) and cfg.repair_units_per_thread in (0, 2, 4)
+    assert {cfg.repair_block_threads, cfg.check_block_threads, cfg.inplace_block_threads} <= {0, 128, 256, 512}
+    want = oracle.to_well_formed_threads(u)
     out.zero_()
     _, fb = pkg.to_well_formed_first_bad(d, out)
-    assert np.array_equal(to_host(out), oracle.to_well_formed_threads(u))
+    assert np.array_equal(to_host(out), want)
     assert int(fb.item()) == oracle.first_bad(u)
+    out.zero_()
+    pkg.to_well_formed(d, out)
+    assert np.array_equal(to_host(out), want)
+    assert pkg.first_error_index_sync(d) == oracle.first_bad(u)
+    out.copy_(d)
+    pkg.to_well_formed_(out)
+    assert np.array_equal(to_host(out), want)
     units, offs = workloads.ragged_batch(count=300_000, seed=52)
     du = to_dev(units)
     do = torch.from_numpy(offs).cuda()
