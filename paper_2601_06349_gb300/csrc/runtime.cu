@@ -188,8 +188,9 @@ int get_ctx(DeviceCtx **out) {
 
 void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) {
     // The out-of-place repair without the first-error index has settings of
-    // its own where they are set (1 GiB at 1e-2: next chunk in flight, 0.953
-    // of the copy peak, against 0.923 with the fused form's plain loads).
+    // its own where they are set: its kernel keeps no first-error state, so
+    // its best shape can differ (1 GiB at 1e-2: 0.95 of the copy peak on its
+    // own tuned settings, 0.92 on the fused form's).
     const bool plain = L.mode == kModeOut && !L.first_bad;
     L.variant = L.mode == kModeCheck     ? cfg.check_variant
                 : L.mode == kModeInPlace ? cfg.inplace_variant
@@ -207,6 +208,7 @@ void configure_single(DeviceCtx *ctx, const utf16_config &cfg, SingleLaunch &L) 
     L.units_per_thread = cfg_u != 0 ? cfg_u : L.n < (long long)ctx->sms * kAutoWideChunkUnitsPerSm ? 2 : 4;
     const bool fb = L.first_bad || L.mode == kModeCheck;
     const bool tma = L.variant == kVariantTma;
+    // Block size: the form's own, else the common one, else kBlockThreads.
     // The TMA kernel's tile is one chunk per warp of a kBlockThreads block.
     const int form_bt = L.mode == kModeCheck     ? cfg.check_block_threads
                         : L.mode == kModeInPlace ? cfg.inplace_block_threads
