@@ -108,6 +108,30 @@ def test_degenerate_batches(pkg):
         _run_all_forms(pkg, u, offs, k % 8, (3 * k) % 8, f"degenerate {k}")
 
 
+def test_string_counts_around_the_lengths_pass(pkg):
+    """The per-string results start from each string's length, which a small
+    kernel writes four strings per thread, 1,024 per block, in one pass of up
+    to four times the batch grid: counts around those sizes, and one just
+    past a full pass (its grid-stride loop then runs twice), with tiny strings
+    so that most strings share a chunk."""
+    import torch
+    rng = np.random.default_rng(17)
+    alph = np.array([0x41, 0xD800, 0xDBFF, 0xDC00, 0xDFFF], np.uint16)
+    # the default check grid is two 512-thread blocks per SM
+    full_pass = 4 * 1024 * 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    for count in (1, 2, 3, 4, 5, 255, 256, 257, 1023, 1024, 1025, 4095, 4096, 4097, full_pass - 1, full_pass,
+                  full_pass + 7):
+        lens = rng.integers(0, 4, count).astype(np.int64)
+        offs = workloads.offsets_from_lengths(lens, start=int(rng.integers(0, 9)))
+        units = alph[rng.integers(0, alph.size, int(offs[-1]) + 3)]
+        d_off = torch.from_numpy(offs).cuda()
+        gi = Guarded(units.size, int(count % 8), units)
+        got = pkg.first_error_index_batch(gi.view, d_off).cpu().numpy()
+        want = oracle.first_bad_batch(units, offs)
+        assert np.array_equal(got, want), (count, first_diff(got, want))
+    pkg.check_device_errors()
+
+
 def test_batch_boundary_pairs(pkg):
     # H | L across a string boundary stays unpaired; inside a string it pairs.
     u = np.array([0x41, 0xD800, 0xDC00, 0xD800, 0xDC00, 0x42] * 1000, np.uint16)
