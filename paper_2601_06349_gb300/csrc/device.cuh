@@ -292,6 +292,24 @@ __device__ __forceinline__ uint4 ld_plain(const uint4 *p) {
 }
 __device__ __forceinline__ void st_stream(uint4 *p, const uint4 &v) { __stcs(p, v); }
 
+// 128-bit load under a predicate instead of a branch: v keeps its value where
+// `take` is false (no memory is touched then).  Loads of several vectors thus
+// all issue before the first is used, where a branch around each would make
+// the merge after it wait for that load.  STREAM: evict-first.
+template <bool STREAM>
+__device__ __forceinline__ void ld_pred(uint4 &v, const uint4 *p, bool take) {
+    if constexpr (STREAM)
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];\n\t}"
+            : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+            : "l"(p), "r"((unsigned)take));
+    else
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q ld.global.v4.u32 {%0,%1,%2,%3}, [%4];\n\t}"
+            : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+            : "l"(p), "r"((unsigned)take));
+}
+
 // Store the 8 units of v at dst, whose alignment is implied by ST (16, 8 or
 // 4 bytes, or 2 = an odd unit index relative to 4 bytes).
 template <int ST>
