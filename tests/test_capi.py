@@ -142,3 +142,38 @@ def test_server_default_options_match_the_header(capi):
         (4 << 30, 1 << 16, 16 << 20, 8, 32 << 20, 256 << 10, 0, 0, 0, 0)
     text = open(os.path.join(HEADER_DIR, "utf16wf.h")).read()
     assert "16 MiB packed per batch, 8 slots, 32 MiB staging" in text
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes through the C ABI has the header's
+    size and field offsets (a C program built with gcc against
+    include/utf16wf.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    import paper_2601_06349_gb300 as pkg
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    pairs = {"utf16_config": pkg.Config, "utf16_server_options": pkg.ServerOptions,
+             "utf16_completion": pkg.Completion, "utf16_server_stats": pkg.ServerStats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "utf16wf.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = {}
+    for line in got:
+        if line:
+            cname, field, value = line.split()
+            seen[(cname, field)] = int(value)
+    for cname, py in pairs.items():
+        assert seen[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert seen[(cname, field)] == getattr(py, field).offset, (cname, field)
