@@ -286,7 +286,8 @@ def test_check_mismatch_at_chunk_edges(pkg, variant, units_per_thread):
 def test_bench_launch_configuration_full_size(pkg):
     """The benchmarked step in the launch configuration the bench uses: the
     autotuner's choice for the 1 GiB string at 1e-2 lone surrogates, then the
-    fused repair, the check and in-place repair, each against the oracle."""
+    fused repair, the check, the repair alone and in-place repair, each
+    against the oracle."""
     import torch
     u = workloads.large_mixed(1e-2)
     want = oracle.to_well_formed_threads(u)
@@ -301,6 +302,10 @@ def test_bench_launch_configuration_full_size(pkg):
         assert np.array_equal(got, want), (cfg.as_dict(), first_diff(got, want))
         assert int(fb.item()) == want_fb
         assert pkg.first_error_index_sync(d_in) == want_fb
+        d_out.zero_()
+        pkg.to_well_formed(d_in, d_out)  # the repair alone, on its own tuned settings
+        got = to_host(d_out)
+        assert np.array_equal(got, want), (cfg.as_dict(), "plain", first_diff(got, want))
         pkg.to_well_formed_(d_in)
         assert np.array_equal(to_host(d_in), want), cfg.as_dict()
         del d_in, d_out
