@@ -41,6 +41,15 @@ struct __align__(16) WordTable {
     uint32_t bad[U * 8];    // the bad words (byte v = vector v's 8 bits) for the block stores
 };
 
+// Bits of the 32-unit word whose first unit is `first` that lie in [0, n).
+__device__ __forceinline__ uint32_t word_inside(long long first, long long n) {
+    const int lo = first >= 0 ? 0 : first < -32 ? 32 : (int)-first;        // units before the string
+    const int hi = n - first <= 0 ? 0 : n - first >= 32 ? 32 : (int)(n - first);  // units up to its end
+    const uint32_t from_lo = lo >= 32 ? 0u : 0xFFFFFFFFu << lo;
+    const uint32_t below_hi = hi >= 32 ? 0xFFFFFFFFu : (1u << hi) - 1u;
+    return from_lo & below_hi;
+}
+
 template <bool FB, int U>
 __device__ __forceinline__ void inplace_words_chunk(const SingleArgs &A, long long cfirst, const Chunk<U> &ch,
                                                     int lane, WordTable<U> &ws, long long &my_first) {
@@ -71,6 +80,10 @@ __device__ __forceinline__ void inplace_words_chunk(const SingleArgs &A, long lo
         L[j] = prmt(t.x, t.y, 0x7531);
         H[j] = s32 & ~L[j];
     }
+    // At an end of the string the units at -1 and n carry the lead and trail
+    // units (a chunk of a longer string sees its neighbours), so the rule can
+    // flag them: only units inside [0, n) are kept.
+    const bool edge = (cfirst < 0) || (cfirst + CU > A.n);
     uint32_t bad[NW];
     int pop = 0;
 #pragma unroll
@@ -83,6 +96,7 @@ __device__ __forceinline__ void inplace_words_chunk(const SingleArgs &A, long lo
         const uint32_t hprev = (H[j] << 1) | h_in;
         const uint32_t lnext = (L[j] >> 1) | (l_in << 31);
         bad[j] = (H[j] & ~lnext) | (L[j] & ~hprev);
+        if (edge) bad[j] &= word_inside(cfirst + 1024 * j + 32 * lane, A.n);
         pop += __popc(bad[j]);
     }
     const unsigned most = __reduce_max_sync(kFull, (unsigned)pop);
@@ -102,8 +116,8 @@ __device__ __forceinline__ void inplace_words_chunk(const SingleArgs &A, long lo
     }
 
     if (A.unit_stores || most <= (unsigned)kSparseMax) {
-        // Units outside the string are never bad (they load as zero), so
-        // every store lands inside it.
+        // Only units inside the string are bad (above), so every store lands
+        // inside it.
 #pragma unroll
         for (int j = 0; j < NW; ++j) {
             uint16_t *base = A.out + cfirst + 1024 * j + 32 * lane;
@@ -119,7 +133,6 @@ __device__ __forceinline__ void inplace_words_chunk(const SingleArgs &A, long lo
 #pragma unroll
     for (int j = 0; j < NW; ++j) ws.bad[32 * j + lane] = bad[j];
     __syncwarp();
-    const bool edge = (cfirst < 0) || (cfirst + CU > A.n);
     const long long lfirst = cfirst + lane * kUnitsPerVec;
     uint16_t *dst = A.out + lfirst;
     const uint8_t *bytes = reinterpret_cast<const uint8_t *>(ws.bad);

@@ -179,14 +179,21 @@ def test_streams_use_independent_slots(pkg):
         assert int(t.item()) == wants[i]
 
 
+@pytest.mark.parametrize("units_per_thread", [0, 4])
 @pytest.mark.parametrize("pageable_direct", ["0", "1"])
 @pytest.mark.parametrize("chunk", [4096, 1 << 20])
-def test_host_pipeline_chunk_edges(pkg, chunk, pageable_direct):
+def test_host_pipeline_chunk_edges(pkg, chunk, pageable_direct, units_per_thread):
     """Pageable host buffers: the staged three-stream pipeline (direct passes
     off), and the direct pass where the device reads pageable memory
-    coherently (else the pipeline again)."""
+    coherently (else the pipeline again).  The pipeline repairs each chunk in
+    place with the units just outside it as neighbours; with 4-vector chunks
+    that is the bit-word kernel, which must not replace those neighbours
+    (surrogate-dense text puts unpaired surrogates on both sides of every
+    chunk edge)."""
     os.environ["UTF16WF_HOST_CHUNK_UNITS"] = str(chunk)
     os.environ["UTF16WF_HOST_PAGEABLE_DIRECT"] = pageable_direct
+    saved = pkg.get_config()
+    pkg.set_config(single_units_per_thread=units_per_thread)
     try:
         for kind, u in (("shifted", workloads.shifted_alternating(3 * chunk + 77)),
                         ("mixed", workloads.mixed(5 * chunk + 3, 0.01, seed=3)),
@@ -201,6 +208,7 @@ def test_host_pipeline_chunk_edges(pkg, chunk, pageable_direct):
     finally:
         os.environ.pop("UTF16WF_HOST_CHUNK_UNITS", None)
         os.environ.pop("UTF16WF_HOST_PAGEABLE_DIRECT", None)
+        pkg.set_config(saved)
 
 
 def test_host_pipeline_pinned_large(pkg):
