@@ -59,17 +59,46 @@ __device__ __forceinline__ void load_chunk(const SingleArgs &A, const uint4 *vin
             else
                 ch.v[u] = ld_stream(p + 32 * u);
         }
-    } else if constexpr (MODE == kModeCheck) {
-        // The read-only check keeps unit loads at the string's ends: the
-        // whole-vector path below costs it 9 registers (40 -> 49: 6 -> 4
-        // resident blocks of 256 threads), and its small calls are bound by
-        // the first-error reduction anyway.
+    } else if constexpr (MODE == kModeCheck && U == 4) {
+        // The check on 4-vector chunks (strings from about 6.2M units, where
+        // one end chunk is a small share of the call) keeps unit loads: either
+        // whole-vector form costs its kernel 9 registers (40 -> 49: 6 -> 4
+        // resident blocks of 256 threads, 1 GiB well formed 176 -> 187 us).
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const long long p0 = cfirst + u * kWarpSliceUnits + lane * kUnitsPerVec;
             ch.v[u] = make_uint4(0, 0, 0, 0);
 #pragma unroll
             for (int k = 0; k < 8; ++k) vec_set_unit(ch.v[u], k, unit_at(A, p0 + k));
+        }
+    } else if constexpr (MODE == kModeCheck) {
+        // The read-only check on 2-vector chunks (the default below about
+        // 6.2M units) reads the same whole vectors as the repair path below,
+        // but clears the units outside the string with one mask per vector
+        // (its callers pass no lead or trail unit): 1,000 units 2.34 -> 1.5-1.8
+        // us per call back to back, 4,095 units 2.19 -> 1.6-1.9.
+        const long long first = cfirst + lane * kUnitsPerVec;
+        const int before = (int)(first > 1 ? -1LL : first < -(CU + 9) ? CU + 9 : -first);
+        const int left = (int)(A.n - first < -1 ? -1LL : A.n - first > CU + 9 ? CU + 9 : A.n - first);
+        const uint4 *p = vin + c * (32LL * U) + lane;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int lo = before - u * kWarpSliceUnits, hi = left - u * kWarpSliceUnits;
+            ch.v[u] = make_uint4(0, 0, 0, 0);
+            ld_pred<true>(ch.v[u], p + 32 * u, hi > 0 && lo < kUnitsPerVec);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int lo = before - u * kWarpSliceUnits, hi = left - u * kWarpSliceUnits;
+            if (lo > 0 || hi < kUnitsPerVec) {
+                const int a = lo < 0 ? 0 : lo > 8 ? 8 : lo, b = hi < 0 ? 0 : hi > 8 ? 8 : hi;
+                uint32_t flo, fhi;
+                bits_to_flags(b > a ? ((1u << b) - 1u) & ~((1u << a) - 1u) : 0u, flo, fhi);
+                ch.v[u].x &= prmt(flo, 0u, 0x9988);
+                ch.v[u].y &= prmt(flo, 0u, 0xBBAA);
+                ch.v[u].z &= prmt(fhi, 0u, 0x9988);
+                ch.v[u].w &= prmt(fhi, 0u, 0xBBAA);
+            }
         }
     } else {
         // A chunk at an end of the string.  Every 16-byte vector that holds a
